@@ -1,0 +1,172 @@
+/*
+ * gj.h -- C ABI of the GB300 epsilon-distance similarity self-join.
+ *
+ * The library finds every ordered pair (a, b) of rows of a point set D whose
+ * Euclidean distance is at most eps (Sec. 3.1, problem statement): dist(a,b) =
+ * sqrt(sum_j (a_j - b_j)^2) <= eps.  Like the paper's result tuples (Sec. 3.2.1:
+ * key/value pairs, one per neighbour of each query point) and its selectivity
+ * S_D = (|R| - |D|)/|D| (Sec. 5.2, Eq. 1), the result R holds both orientations
+ * (a,b) and (b,a) of every pair and the |D| self-pairs (a,a).
+ *
+ * Method (Alg. 1): REORDER dimensions by variance (Sec. 4.2); build a grid
+ * index of eps-wide cells over the first k reordered dimensions, non-empty
+ * cells only, linearised and sorted (Sec. 3.2.1, 4.1); search the 3^k adjacent
+ * cells of each query cell (Sec. 3.2.1, Fig. 1), optionally narrowed by a
+ * window on one un-indexed dimension (SORTIDU, Sec. 4.3); compute FP64 squared
+ * distances that stop once the running sum exceeds eps^2 (SHORTC, Sec. 4.4);
+ * emit pairs in result-set batches (Sec. 3.2.2) over a work queue ordered by
+ * estimated cell load.  Every stage runs as CUDA kernels on one GPU.
+ *
+ * Exactness.  A pair is reported iff its FP64 squared distance, summed over
+ * the reordered dimensions, is <= fl(eps*eps).  The summation order (reordered
+ * dimensions, fused multiply-add) differs from the original-order sum only in
+ * the last bits, so the result can differ from an original-order reference
+ * only for pairs whose squared distance lies within ~d*2^-53 relative of eps^2.
+ *
+ * Threading: a handle is used by one host thread at a time.  Status codes are
+ * returned by value; gj_index_build returns NULL and leaves its status in a
+ * thread-local slot read by gj_last_status().
+ */
+#ifndef GJ_H
+#define GJ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------- */
+#define GJ_OK                 0
+#define GJ_ERR_INVALID_ARG   -1  /* n < 0, d < 1, eps <= 0 or NaN, k out of range, NULL handle ... */
+#define GJ_ERR_NONFINITE     -2  /* a coordinate is NaN or infinite                                  */
+#define GJ_ERR_OOM           -3  /* device or pinned host allocation failed                          */
+#define GJ_ERR_CUDA          -4  /* a CUDA runtime call or kernel launch failed                      */
+#define GJ_ERR_CAPACITY      -5  /* |R| > cap: *count holds |R|, the output holds cap pairs (unordered) */
+#define GJ_ERR_TIMEOUT       -6  /* a bounded device-side wait ran out; the context stays usable     */
+#define GJ_ERR_UNSUPPORTED   -7  /* no usable device (needs compute capability 10.3, sm_103a)        */
+#define GJ_ERR_TOO_LARGE     -8  /* n >= 2^32 (pair ids are 32-bit) or d > GJ_MAX_DIMS               */
+
+#define GJ_MAX_DIMS 1024
+
+/* ---- flags (gj_config.flags) -------------------------------------------- */
+#define GJ_REORDER    (1u << 0)  /* Sec. 4.2: index the k highest-variance dimensions       */
+#define GJ_SORTIDU    (1u << 1)  /* Sec. 4.3: sort cells by one un-indexed dim, window search */
+#define GJ_SHORTC     (1u << 2)  /* Sec. 4.4: stop a distance once it exceeds eps^2          */
+#define GJ_TC_FILTER  (1u << 3)  /* tensor-core candidate filter + exact FP64 recheck (no paper counterpart) */
+#define GJ_DEFAULT_FLAGS (GJ_REORDER | GJ_SORTIDU | GJ_SHORTC)
+
+/* One result pair: original row indices of the two points. */
+typedef struct {
+    uint32_t a, b;
+} gj_pair;
+
+/* Opaque index handle (library-owned device memory). */
+typedef struct gj_index gj_index;
+
+/* Build options.  Zero-initialise, then set what you need; gj_config_init
+ * fills the defaults. */
+typedef struct {
+    int32_t  k;           /* indexed dimensions: 0 = choose automatically; else 1..min(d,8)      */
+    uint32_t flags;       /* GJ_* flags; gj_config_init sets GJ_DEFAULT_FLAGS                     */
+    void    *stream;      /* cudaStream_t to run on; NULL = a stream the handle creates             */
+    uint64_t batch_pairs; /* result batch size b_s in pairs; 0 = the rule of Sec. 3.2.2           */
+    int32_t  device;      /* CUDA device ordinal; -1 = the calling thread's current device        */
+    uint32_t reserved[7];
+} gj_config;
+
+/* Read-only facts about a built index. */
+typedef struct {
+    int64_t  n;
+    int32_t  d;
+    int32_t  k;              /* indexed dimensions actually used                                 */
+    double   eps;
+    int64_t  nonempty_cells; /* |G| (Sec. 3.2.1)                                                  */
+    int64_t  work_items;     /* query blocks in the load-ordered work queue                     */
+    uint64_t candidate_pairs;/* unordered candidate pairs i<j in adjacent cells (no SORTIDU)     */
+    uint64_t window_pairs;   /* unordered candidate pairs left after the SORTIDU window          */
+    uint32_t flags;
+    int32_t  sortidu_dim;    /* reordered index of the SORTIDU dimension, -1 if off             */
+    int32_t  perm[GJ_MAX_DIMS]; /* REORDER: perm[r] = original index of reordered dimension r   */
+} gj_index_info_t;
+
+/* Per-call measurements of the last gj_self_join on a handle. */
+typedef struct {
+    uint64_t pairs;          /* |R|                                                               */
+    uint32_t launches;       /* join kernel launches (result batches + overflow resumes)          */
+    uint32_t batches_planned;/* n_b from the sampled estimate (Sec. 3.2.2)                       */
+    uint64_t batch_pairs;    /* b_s used                                                         */
+    uint64_t estimate;       /* sampled |R| estimate                                             */
+    uint64_t tc_survivors;   /* GJ_TC_FILTER: candidates passed to the FP64 recheck             */
+    double   join_ms;        /* device time of the join kernels (CUDA events)                   */
+    double   total_ms;       /* host wall time of the call                                       */
+} gj_join_stats;
+
+/* Fill *cfg with defaults (k = 0, GJ_DEFAULT_FLAGS, own stream, paper batch rule). */
+void gj_config_init(gj_config *cfg);
+
+/*
+ * Build the index of Alg. 1 (REORDER, constructIndex) for n points of d
+ * dimensions.
+ *   points  row-major n x d FP64, in host memory (pageable or pinned) or in
+ *           device memory of the chosen device; detected with
+ *           cudaPointerGetAttributes.  It is copied; the caller keeps ownership
+ *           and may free or change it after the call returns.
+ *   n       number of points, 0 <= n < 2^32.
+ *   d       dimensions, 1 <= d <= GJ_MAX_DIMS.
+ *   eps     search distance, finite and > 0.
+ *   k       indexed dimensions: 0 = choose automatically (Sec. 4.1 trade-off),
+ *           else 1 <= k <= min(d, 8).  The library may index fewer dimensions
+ *           than asked when the linear cell id would not fit in 62 bits; the
+ *           pair set never depends on k.
+ * Returns a handle, or NULL with the reason in gj_last_status().
+ */
+gj_index *gj_index_build(const double *points, int64_t n, int32_t d, double eps, int32_t k);
+gj_index *gj_index_build_ex(const double *points, int64_t n, int32_t d, double eps,
+                            const gj_config *cfg);
+
+/*
+ * The self-join (Alg. 1, batch loop and SelfJoinKernel): writes R into
+ * pairs_out in no particular order.
+ *   pairs_out  host memory (pageable or pinned) or device memory for cap pairs;
+ *              may be NULL only when cap == 0 (count-only query).
+ *   cap        capacity of pairs_out in pairs.
+ *   count      out: |R| (always the full size, also on GJ_ERR_CAPACITY).
+ * Returns GJ_OK, or GJ_ERR_CAPACITY when |R| > cap (pairs_out then holds cap
+ * pairs of R, an unspecified subset), or another error code.
+ */
+int gj_self_join(gj_index *h, gj_pair *pairs_out, uint64_t cap, uint64_t *count);
+
+/*
+ * Entity partitioning (Sec. 6.2): the part of R whose first point lies in
+ * query set l of N_b, where the load-ordered query blocks are dealt to the N_b
+ * sets round-robin.  The union over l = 0..N_b-1 is R, each pair exactly once.
+ * Semantics of pairs_out/cap/count as in gj_self_join.
+ */
+int gj_self_join_part(gj_index *h, int32_t part, int32_t nparts, gj_pair *pairs_out,
+                      uint64_t cap, uint64_t *count);
+
+/* Facts about the index (k used, REORDER permutation, cell and candidate counts). */
+int gj_index_get_info(const gj_index *h, gj_index_info_t *info);
+
+/* Measurements of the last join on this handle. */
+int gj_last_join_stats(const gj_index *h, gj_join_stats *st);
+
+/* Release the handle and its device memory.  NULL-safe. */
+void gj_free(gj_index *h);
+
+/* Status of the last gj_index_build* on this thread. */
+int gj_last_status(void);
+
+/* Static English text for a status code. */
+const char *gj_status_string(int status);
+
+/* Library version, "major.minor.patch". */
+const char *gj_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GJ_H */
