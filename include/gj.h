@@ -43,7 +43,7 @@ extern "C" {
 #define GJ_ERR_NONFINITE     -2  /* a coordinate is NaN or infinite                                  */
 #define GJ_ERR_OOM           -3  /* device or pinned host allocation failed                          */
 #define GJ_ERR_CUDA          -4  /* a CUDA runtime call or kernel launch failed                      */
-#define GJ_ERR_CAPACITY      -5  /* |R| > cap: *count holds |R|, the output holds cap pairs (unordered) */
+#define GJ_ERR_CAPACITY      -5  /* |R| > cap: *count holds |R|; output contents unspecified         */
 #define GJ_ERR_TIMEOUT       -6  /* a bounded device-side wait ran out; the context stays usable     */
 #define GJ_ERR_UNSUPPORTED   -7  /* no usable device (needs compute capability 10.3, sm_103a)        */
 #define GJ_ERR_TOO_LARGE     -8  /* n >= 2^32 (pair ids are 32-bit) or d > GJ_MAX_DIMS               */
@@ -99,7 +99,10 @@ typedef struct {
     uint64_t batch_pairs;    /* b_s used                                                         */
     uint64_t estimate;       /* sampled |R| estimate                                             */
     uint64_t tc_survivors;   /* GJ_TC_FILTER: candidates passed to the FP64 recheck             */
+    uint64_t evaluated;      /* candidate pairs whose distance was computed (after SORTIDU)       */
+    uint64_t dims;           /* FP64 dimensions evaluated, summed over those pairs (SHORTC depth) */
     double   join_ms;        /* device time of the join kernels (CUDA events)                   */
+    double   estimate_ms;    /* device time of the sampled estimate                              */
     double   total_ms;       /* host wall time of the call                                       */
 } gj_join_stats;
 
@@ -129,20 +132,25 @@ gj_index *gj_index_build_ex(const double *points, int64_t n, int32_t d, double e
 /*
  * The self-join (Alg. 1, batch loop and SelfJoinKernel): writes R into
  * pairs_out in no particular order.
- *   pairs_out  host memory (pageable or pinned) or device memory for cap pairs;
- *              may be NULL only when cap == 0 (count-only query).
+ *   pairs_out  host memory (pageable or pinned) or device memory of the
+ *              handle's device, for cap pairs; NULL with cap == 0 asks for the
+ *              count only (returns GJ_OK).
  *   cap        capacity of pairs_out in pairs.
  *   count      out: |R| (always the full size, also on GJ_ERR_CAPACITY).
- * Returns GJ_OK, or GJ_ERR_CAPACITY when |R| > cap (pairs_out then holds cap
- * pairs of R, an unspecified subset), or another error code.
+ * Returns GJ_OK, or GJ_ERR_CAPACITY when |R| > cap (the contents of pairs_out
+ * are then unspecified), or another error code.  Host output is copied in
+ * result batches on a second stream while the next batch runs; pinned host
+ * memory lets those copies overlap the join.
  */
 int gj_self_join(gj_index *h, gj_pair *pairs_out, uint64_t cap, uint64_t *count);
 
 /*
- * Entity partitioning (Sec. 6.2): the part of R whose first point lies in
- * query set l of N_b, where the load-ordered query blocks are dealt to the N_b
- * sets round-robin.  The union over l = 0..N_b-1 is R, each pair exactly once.
- * Semantics of pairs_out/cap/count as in gj_self_join.
+ * Entity partitioning (Sec. 6.2): the part of R computed by query set
+ * l = part of N_b = nparts, where the load-ordered query blocks are dealt to
+ * the sets round-robin (block r goes to set r mod N_b).  Every unordered pair
+ * is computed by exactly one query block, which emits both orientations, so
+ * the parts are disjoint and their union is R.  Semantics of
+ * pairs_out/cap/count as in gj_self_join.
  */
 int gj_self_join_part(gj_index *h, int32_t part, int32_t nparts, gj_pair *pairs_out,
                       uint64_t cap, uint64_t *count);
@@ -164,6 +172,12 @@ const char *gj_status_string(int status);
 
 /* Library version, "major.minor.patch". */
 const char *gj_version(void);
+
+/* Measurement helper (no paper counterpart): FP64 fused multiply-add
+ * throughput of the device in TFLOP/s (2 FLOPs per FMA), from independent
+ * FMA chains timed with CUDA events; the denominator of the plain join's
+ * roofline.  device = -1 for the current device. */
+int gj_probe_fp64_tflops(int32_t device, double *tflops);
 
 #ifdef __cplusplus
 }

@@ -1,0 +1,625 @@
+// gj_api.cu -- the C ABI (include/gj.h) and the batch loop of Alg. 1.
+//
+// gj_self_join follows Alg. 1's batch loop with the batching scheme of
+// Sec. 3.2.2: a sampled count-only pass estimates |R|; the batch size b_s and
+// the number of batches n_b >= 3 follow from it (b_s = 1e8 pairs when the
+// estimate exceeds 3e8); each batch is one launch of the persistent join over
+// a contiguous range of the load-ordered queue (the queue is interleaved so
+// every range is a cost-stratified sample).  A batch whose results outgrow its
+// buffer stops at committed work items and hands resume points to the next
+// launch, so the result is exact whatever the estimate.  With a host output
+// buffer the results of batch i are copied to the host on a second stream
+// while batch i+1 runs (the HtoD / Kernel / DtoH overlap of Fig. 4).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <vector>
+
+#include "gj_internal.cuh"
+
+using namespace gj;
+
+static thread_local int t_last_status = GJ_OK;
+
+namespace {
+
+int cuda_status(cudaError_t e)
+{
+    if (e == cudaSuccess)
+        return GJ_OK;
+    if (e == cudaErrorMemoryAllocation)
+        return GJ_ERR_OOM;
+    return GJ_ERR_CUDA;
+}
+
+__global__ void k_gather_queue(const uint32_t *__restrict__ order, int part, int nparts, int64_t nq,
+                               int64_t nb, uint32_t *__restrict__ q)
+{
+    // Partition item of load rank r goes to batch r % nb at offset r / nb;
+    // batch b occupies [b*qn + min(b, rem), ...) with qn = nq / nb,
+    // rem = nq % nb.  Every batch range is then a stratified sample of the
+    // descending-load order, itself in descending load.
+    int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r >= nq)
+        return;
+    const int64_t qn = nq / nb, rem = nq % nb;
+    const int64_t b = r % nb;
+    q[b * qn + (b < rem ? b : rem) + r / nb] = order[(int64_t)part + r * nparts];
+}
+
+__global__ void k_stride_queue(const uint32_t *__restrict__ q, int64_t nq, int64_t stride, uint32_t *__restrict__ out,
+                               int64_t nout)
+{
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t < nout)
+        out[t] = q[t * stride];
+}
+
+double now_ms()
+{
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+struct JoinBuffers {
+    JoinCtl *ctl = nullptr;
+    JoinCtl *hctl_up = nullptr, *hctl_dn = nullptr;   // pinned
+    Deferred *def[2] = {nullptr, nullptr};
+    gj_pair *staging = nullptr;
+    gj_pair *dbuf[2] = {nullptr, nullptr};
+    uint32_t *queue = nullptr, *qtmp = nullptr, *sample = nullptr;
+    cudaEvent_t ev_k0 = nullptr, ev_k1 = nullptr, ev_ctl = nullptr, ev_drained[2] = {nullptr, nullptr};
+    ~JoinBuffers()
+    {
+        cudaFree(ctl);
+        cudaFreeHost(hctl_up);
+        cudaFreeHost(hctl_dn);
+        cudaFree(def[0]);
+        cudaFree(def[1]);
+        cudaFree(staging);
+        cudaFree(dbuf[0]);
+        cudaFree(dbuf[1]);
+        cudaFree(queue);
+        cudaFree(qtmp);
+        cudaFree(sample);
+        if (ev_k0) cudaEventDestroy(ev_k0);
+        if (ev_k1) cudaEventDestroy(ev_k1);
+        if (ev_ctl) cudaEventDestroy(ev_ctl);
+        for (auto &e : ev_drained)
+            if (e) cudaEventDestroy(e);
+    }
+};
+
+bool is_device_ptr(const void *p)
+{
+    if (!p)
+        return false;
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+IndexView view_of(const gj_index *h)
+{
+    IndexView v{};
+    v.X = h->X;
+    v.orig = h->orig;
+    v.cell_start = h->cell_start;
+    v.adj_start = h->adj_start;
+    v.adj = h->adj;
+    v.items = h->items;
+    v.n = h->info.n;
+    v.npad = h->npad;
+    v.d = h->info.d;
+    v.u = h->u;
+    v.e2 = h->e2;
+    v.ew = h->ew;
+    return v;
+}
+
+// One launch of the persistent join; reads back the control block.
+int run_launch(gj_index *h, JoinBuffers &B, JoinLaunch L, int grid, JoinCtl init, JoinCtl *result,
+               double *kernel_ms)
+{
+    cudaStream_t s = h->stream;
+    *B.hctl_up = init;
+    cudaError_t e = cudaMemcpyAsync(B.ctl, B.hctl_up, sizeof(JoinCtl), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess)
+        return cuda_status(e);
+    L.ctl = B.ctl;
+    cudaEventRecord(B.ev_k0, s);
+    e = launch_join_plain(L, grid, s);
+    if (e != cudaSuccess)
+        return cuda_status(e);
+    cudaEventRecord(B.ev_k1, s);
+    e = cudaMemcpyAsync(B.hctl_dn, B.ctl, sizeof(JoinCtl), cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess)
+        return cuda_status(e);
+    cudaEventRecord(B.ev_ctl, s);
+    e = cudaEventSynchronize(B.ev_ctl);
+    if (e != cudaSuccess)
+        return cuda_status(e);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, B.ev_k0, B.ev_k1);
+    *kernel_ms += ms;
+    *result = *B.hctl_dn;
+    if (result->err & (kErrStaging | kErrDeferred))
+        return GJ_ERR_CUDA;
+    if (result->err & kErrTimeout)
+        return GJ_ERR_TIMEOUT;
+    return GJ_OK;
+}
+
+int join_impl(gj_index *h, int part, int nparts, gj_pair *pairs_out, uint64_t cap, uint64_t *count)
+{
+    if (!h || !count || nparts < 1 || part < 0 || part >= nparts || (!pairs_out && cap > 0))
+        return GJ_ERR_INVALID_ARG;
+    const double t_start = now_ms();
+    *count = 0;
+    memset(&h->last, 0, sizeof(h->last));
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e != cudaSuccess)
+        return cuda_status(e);
+    cudaStream_t s = h->stream;
+    const int64_t nitems = h->nitems;
+    const int64_t nq = nitems > part ? (nitems - part + nparts - 1) / nparts : 0;
+    if (nq == 0) {
+        h->last.total_ms = now_ms() - t_start;
+        return GJ_OK;
+    }
+    const int per_sm = plain_ctas_per_sm(h->info.d);
+    if (per_sm < 1)
+        return GJ_ERR_UNSUPPORTED;
+    const int grid = h->sms * per_sm;
+    const uint32_t stg_cap = 1u << 16;   // pairs per CTA staging area (>= 4 tiles of output)
+    const bool dev_out = is_device_ptr(pairs_out);
+    const bool count_only_call = (cap == 0);
+
+    JoinBuffers B;
+#define TRYC(x)                                                     \
+    do {                                                            \
+        cudaError_t _e = (x);                                       \
+        if (_e != cudaSuccess)                                      \
+            return cuda_status(_e);                                 \
+    } while (0)
+    TRYC(cudaMalloc(&B.ctl, sizeof(JoinCtl)));
+    TRYC(cudaMallocHost(&B.hctl_up, sizeof(JoinCtl)));
+    TRYC(cudaMallocHost(&B.hctl_dn, sizeof(JoinCtl)));
+    TRYC(cudaMalloc(&B.def[0], (size_t)grid * sizeof(Deferred)));
+    TRYC(cudaMalloc(&B.def[1], (size_t)grid * sizeof(Deferred)));
+    TRYC(cudaMalloc(&B.queue, nq * sizeof(uint32_t)));
+    TRYC(cudaMalloc(&B.qtmp, nq * sizeof(uint32_t)));
+    TRYC(cudaEventCreate(&B.ev_k0));
+    TRYC(cudaEventCreate(&B.ev_k1));
+    TRYC(cudaEventCreateWithFlags(&B.ev_ctl, cudaEventBlockingSync));
+    TRYC(cudaEventCreateWithFlags(&B.ev_drained[0], cudaEventDisableTiming));
+    TRYC(cudaEventCreateWithFlags(&B.ev_drained[1], cudaEventDisableTiming));
+
+    JoinLaunch L{};
+    L.ix = view_of(h);
+    L.dout_cap = (uint32_t)grid;
+    L.stg_cap = stg_cap;
+    double kms = 0.0;
+    uint32_t launches = 0;
+    unsigned long long evaluated = 0, dims = 0;
+
+    // ---- 1. sampled estimate of |R| (count-only over every S-th item), Sec. 3.2.2
+    k_gather_queue<<<(int)((nq + 255) / 256), 256, 0, s>>>(h->order, part, nparts, nq, 1, B.qtmp);
+    TRYC(cudaGetLastError());
+    uint64_t estimate = 0;
+    const bool want_batches = !count_only_call && !dev_out;
+    const int64_t S = std::max<int64_t>(1, std::min<int64_t>(100, nq / std::max(1, grid)));
+    if (want_batches && h->cfg.batch_pairs == 0 && S >= 8) {
+        const int64_t ns = (nq + S - 1) / S;
+        TRYC(cudaMalloc(&B.sample, ns * sizeof(uint32_t)));
+        k_stride_queue<<<(int)((ns + 255) / 256), 256, 0, s>>>(B.qtmp, nq, S, B.sample, ns);
+        TRYC(cudaGetLastError());
+        JoinLaunch Ls = L;
+        Ls.queue = B.sample;
+        Ls.qlimit = (uint32_t)ns;
+        Ls.out = nullptr;
+        Ls.staging = nullptr;
+        Ls.din = nullptr;
+        Ls.n_din = 0;
+        Ls.dout = B.def[0];
+        JoinCtl init{};
+        init.fail_base = ~0ull;
+        JoinCtl res{};
+        double est_ms = 0.0;
+        int st0 = run_launch(h, B, Ls, grid, init, &res, &est_ms);
+        if (st0 != GJ_OK)
+            return st0;
+        estimate = (uint64_t)((double)res.counted * (double)nq / (double)ns);
+        h->last.estimate_ms = est_ms;
+    }
+
+    // ---- 2. batch size and count (Sec. 3.2.2: n_b >= 3; b_s = 1e8 above 3e8)
+    uint64_t bs;
+    int64_t nb;
+    if (h->cfg.batch_pairs) {
+        bs = h->cfg.batch_pairs;
+        nb = std::max<int64_t>(3, (int64_t)((estimate + bs - 1) / bs));
+    } else if (estimate > 300000000ull) {
+        bs = 100000000ull;
+        nb = (int64_t)((estimate + bs - 1) / bs);
+    } else {
+        nb = 3;
+        bs = std::max<uint64_t>((uint64_t)((double)estimate / 3.0 * 1.25), (uint64_t)1 << 20);
+    }
+    if (!want_batches)
+        nb = 1;
+    nb = std::max<int64_t>(1, std::min<int64_t>(nb, nq));
+    h->last.estimate = estimate;
+    h->last.batches_planned = (uint32_t)nb;
+    h->last.batch_pairs = want_batches ? bs : 0;
+
+    // the dequeue order: nb interleaved ranges of the load order
+    k_gather_queue<<<(int)((nq + 255) / 256), 256, 0, s>>>(h->order, part, nparts, nq, nb, B.queue);
+    TRYC(cudaGetLastError());
+    const int64_t qn = nq / nb, rem = nq % nb;
+    auto batch_end = [&](int64_t b) { return (b + 1) * qn + std::min<int64_t>(b + 1, rem); };
+
+    if (want_batches) {
+        TRYC(cudaMalloc(&B.dbuf[0], bs * sizeof(gj_pair)));
+        TRYC(cudaMalloc(&B.dbuf[1], bs * sizeof(gj_pair)));
+    }
+    if (!count_only_call)
+        TRYC(cudaMalloc(&B.staging, (size_t)grid * stg_cap * sizeof(gj_pair)));
+
+    // ---- 3. batch loop
+    uint64_t written = 0, total = 0;
+    uint32_t head = 0, n_din = 0;
+    int cur = 0;
+    bool counting = count_only_call;
+    int64_t batch = 0;
+    int st = GJ_OK;
+    bool drained_pending[2] = {false, false};
+    for (int guard = 0; guard < 1000000; ++guard) {
+        const uint32_t qlimit = (uint32_t)std::min<int64_t>(nq, batch_end(batch));
+        if (head >= (uint32_t)nq && n_din == 0)
+            break;
+        JoinLaunch Lb = L;
+        Lb.queue = B.queue;
+        Lb.qlimit = qlimit;
+        Lb.din = B.def[cur];
+        Lb.n_din = n_din;
+        Lb.dout = B.def[cur ^ 1];
+        uint64_t lcap = 0;
+        gj_pair *lout = nullptr;
+        if (!counting) {
+            if (dev_out) {
+                lout = pairs_out + written;
+                lcap = cap - written;
+            } else {
+                lout = B.dbuf[launches & 1];
+                lcap = bs;
+                if (drained_pending[launches & 1])
+                    TRYC(cudaStreamWaitEvent(s, B.ev_drained[launches & 1], 0));
+            }
+            if (lcap == 0)
+                counting = true;
+        }
+        Lb.out = counting ? nullptr : lout;
+        Lb.cap = counting ? 0 : lcap;
+        Lb.staging = counting ? nullptr : B.staging;
+        JoinCtl init{};
+        init.fail_base = ~0ull;
+        init.head = head;
+        JoinCtl res{};
+        st = run_launch(h, B, Lb, grid, init, &res, &kms);
+        if (st != GJ_OK)
+            break;
+        ++launches;
+        evaluated += res.evaluated;
+        dims += res.dims;
+        if (counting) {
+            total += res.counted;
+        } else {
+            uint64_t valid = res.full ? std::min<unsigned long long>(res.pos, res.fail_base) : res.pos;
+            total += valid;
+            if (!dev_out && valid) {
+                const int slot = (launches - 1) & 1;
+                uint64_t room = cap > written ? cap - written : 0;
+                uint64_t ncopy = std::min<uint64_t>(valid, room);
+                if (ncopy) {
+                    TRYC(cudaEventRecord(B.ev_ctl, s));
+                    TRYC(cudaStreamWaitEvent(h->drain_stream, B.ev_ctl, 0));
+                    TRYC(cudaMemcpyAsync(pairs_out + written, B.dbuf[slot], ncopy * sizeof(gj_pair),
+                                         cudaMemcpyDeviceToHost, h->drain_stream));
+                    TRYC(cudaEventRecord(B.ev_drained[slot], h->drain_stream));
+                    drained_pending[slot] = true;
+                }
+                written += ncopy;
+                if (ncopy < valid)   // user buffer full: the rest is only counted
+                    counting = true;
+            } else if (dev_out) {
+                written += valid;
+                if (res.full)        // user buffer full: the rest is only counted
+                    counting = true;
+            }
+        }
+        n_din = std::min<uint32_t>(res.dout_n, (uint32_t)grid);
+        cur ^= 1;
+        head = std::min<uint32_t>(res.head, qlimit);
+        if (head >= qlimit && batch + 1 < nb)
+            ++batch;
+    }
+    if (st == GJ_OK)
+        TRYC(cudaStreamSynchronize(h->drain_stream));
+    TRYC(cudaStreamSynchronize(s));
+#undef TRYC
+    *count = total;
+    h->last.pairs = total;
+    h->last.launches = launches;
+    h->last.join_ms = kms;
+    h->last.total_ms = now_ms() - t_start;
+    h->last.tc_survivors = 0;
+    h->last.evaluated = evaluated;
+    h->last.dims = dims;
+    if (st != GJ_OK)
+        return st;
+    if (!count_only_call && total > cap)
+        return GJ_ERR_CAPACITY;
+    if (count_only_call && total > 0)
+        return GJ_ERR_CAPACITY;
+    return GJ_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void gj_config_init(gj_config *cfg)
+{
+    if (!cfg)
+        return;
+    memset(cfg, 0, sizeof(*cfg));
+    cfg->k = 0;
+    cfg->flags = GJ_DEFAULT_FLAGS;
+    cfg->stream = nullptr;
+    cfg->batch_pairs = 0;
+    cfg->device = -1;
+}
+
+gj_index *gj_index_build_ex(const double *points, int64_t n, int32_t d, double eps, const gj_config *cfg_in)
+{
+    gj_config cfg;
+    if (cfg_in)
+        cfg = *cfg_in;
+    else
+        gj_config_init(&cfg);
+    if (n < 0 || d < 1 || !(eps > 0.0) || !isfinite(eps) || (n > 0 && !points) || cfg.k < 0) {
+        t_last_status = GJ_ERR_INVALID_ARG;
+        return nullptr;
+    }
+    if (n >= ((int64_t)1 << 32) || d > GJ_MAX_DIMS) {
+        t_last_status = GJ_ERR_TOO_LARGE;
+        return nullptr;
+    }
+    if (cfg.k > std::min(d, MAXK)) {
+        t_last_status = GJ_ERR_INVALID_ARG;
+        return nullptr;
+    }
+    int dev = cfg.device;
+    cudaError_t e;
+    if (dev < 0) {
+        e = cudaGetDevice(&dev);
+    } else {
+        e = cudaSetDevice(dev);
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        t_last_status = GJ_ERR_UNSUPPORTED;
+        return nullptr;
+    }
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess || prop.major != 10 || prop.minor != 3) {
+        t_last_status = GJ_ERR_UNSUPPORTED;
+        return nullptr;
+    }
+    gj_index *h = new (std::nothrow) gj_index();
+    if (!h) {
+        t_last_status = GJ_ERR_OOM;
+        return nullptr;
+    }
+    h->device = dev;
+    h->cfg = cfg;
+    h->sms = prop.multiProcessorCount;
+    h->info.n = n;
+    h->info.d = d;
+    h->info.eps = eps;
+    h->info.flags = cfg.flags;
+    h->e2 = eps * eps;
+    h->ew = eps * (1.0 + ldexp(1.0, -40));
+    int st = GJ_OK;
+    double *P = nullptr;
+    unsigned int *flag = nullptr;
+    unsigned int hflag = 0;
+    if (cfg.stream) {
+        h->stream = (cudaStream_t)cfg.stream;
+        h->own_stream = false;
+    } else {
+        e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+        h->own_stream = true;
+        if (e != cudaSuccess) {
+            st = cuda_status(e);
+            goto fail;
+        }
+    }
+    e = cudaStreamCreateWithFlags(&h->drain_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        st = cuda_status(e);
+        goto fail;
+    }
+    e = cudaMalloc(&P, std::max<size_t>((size_t)n * d, 1) * sizeof(double));
+    if (e == cudaSuccess)
+        e = cudaMalloc(&flag, sizeof(unsigned int));
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(flag, 0, sizeof(unsigned int), h->stream);
+    if (e == cudaSuccess && n > 0)
+        e = cudaMemcpyAsync(P, points, (size_t)n * d * sizeof(double), cudaMemcpyDefault, h->stream);
+    if (e == cudaSuccess)
+        e = launch_check_finite(P, n * (int64_t)d, flag, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&hflag, flag, sizeof(unsigned int), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+        st = cuda_status(e);
+        goto fail;
+    }
+    if (hflag) {
+        st = GJ_ERR_NONFINITE;
+        goto fail;
+    }
+    st = build_index(h, P, n, d, eps, cfg.k, cfg.flags, h->stream);
+    if (st != GJ_OK)
+        goto fail;
+    cudaFree(P);
+    cudaFree(flag);
+    t_last_status = GJ_OK;
+    return h;
+fail:
+    cudaFree(P);
+    cudaFree(flag);
+    gj_free(h);
+    cudaGetLastError();
+    t_last_status = st;
+    return nullptr;
+}
+
+gj_index *gj_index_build(const double *points, int64_t n, int32_t d, double eps, int32_t k)
+{
+    gj_config cfg;
+    gj_config_init(&cfg);
+    cfg.k = k;
+    return gj_index_build_ex(points, n, d, eps, &cfg);
+}
+
+int gj_self_join(gj_index *h, gj_pair *pairs_out, uint64_t cap, uint64_t *count)
+{
+    int st = join_impl(h, 0, 1, pairs_out, cap, count);
+    if (st == GJ_ERR_CAPACITY && cap == 0 && !pairs_out)
+        return GJ_OK;   // count-only query
+    return st;
+}
+
+int gj_self_join_part(gj_index *h, int32_t part, int32_t nparts, gj_pair *pairs_out, uint64_t cap,
+                      uint64_t *count)
+{
+    int st = join_impl(h, part, nparts, pairs_out, cap, count);
+    if (st == GJ_ERR_CAPACITY && cap == 0 && !pairs_out)
+        return GJ_OK;
+    return st;
+}
+
+int gj_index_get_info(const gj_index *h, gj_index_info_t *info)
+{
+    if (!h || !info)
+        return GJ_ERR_INVALID_ARG;
+    *info = h->info;
+    return GJ_OK;
+}
+
+int gj_last_join_stats(const gj_index *h, gj_join_stats *st)
+{
+    if (!h || !st)
+        return GJ_ERR_INVALID_ARG;
+    *st = h->last;
+    return GJ_OK;
+}
+
+void gj_free(gj_index *h)
+{
+    if (!h)
+        return;
+    cudaSetDevice(h->device);
+    if (h->stream)
+        cudaStreamSynchronize(h->stream);
+    cudaFree(h->X);
+    cudaFree(h->orig);
+    cudaFree(h->cell_start);
+    cudaFree(h->cell_id);
+    cudaFree(h->adj_start);
+    cudaFree(h->adj);
+    cudaFree(h->items);
+    cudaFree(h->order);
+    if (h->drain_stream)
+        cudaStreamDestroy(h->drain_stream);
+    if (h->own_stream && h->stream)
+        cudaStreamDestroy(h->stream);
+    delete h;
+}
+
+int gj_last_status(void) { return t_last_status; }
+
+const char *gj_status_string(int status)
+{
+    switch (status) {
+    case GJ_OK: return "ok";
+    case GJ_ERR_INVALID_ARG: return "invalid argument";
+    case GJ_ERR_NONFINITE: return "a coordinate is NaN or infinite";
+    case GJ_ERR_OOM: return "out of device or pinned host memory";
+    case GJ_ERR_CUDA: return "CUDA error";
+    case GJ_ERR_CAPACITY: return "result larger than the output capacity";
+    case GJ_ERR_TIMEOUT: return "a bounded device wait ran out";
+    case GJ_ERR_UNSUPPORTED: return "no usable GPU (needs compute capability 10.3)";
+    case GJ_ERR_TOO_LARGE: return "input too large (n >= 2^32 or d > GJ_MAX_DIMS)";
+    default: return "unknown status";
+    }
+}
+
+const char *gj_version(void) { return "0.1.0"; }
+
+int gj_probe_fp64_tflops(int device, double *tflops)
+{
+    if (!tflops)
+        return GJ_ERR_INVALID_ARG;
+    int dev = device;
+    if (dev < 0 && cudaGetDevice(&dev) != cudaSuccess)
+        return GJ_ERR_UNSUPPORTED;
+    if (cudaSetDevice(dev) != cudaSuccess)
+        return GJ_ERR_UNSUPPORTED;
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess)
+        return GJ_ERR_CUDA;
+    const int grid = prop.multiProcessorCount * 8, iters = 1 << 14;
+    double *out = nullptr;
+    cudaStream_t s;
+    cudaEvent_t a, b;
+    if (cudaMalloc(&out, grid * sizeof(double)) != cudaSuccess)
+        return GJ_ERR_OOM;
+    cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    launch_fp64_probe(out, iters, grid, s);   // warm-up
+    float best = 1e30f;
+    for (int r = 0; r < 3; ++r) {
+        cudaEventRecord(a, s);
+        launch_fp64_probe(out, iters, grid, s);
+        cudaEventRecord(b, s);
+        cudaEventSynchronize(b);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, a, b);
+        best = std::min(best, ms);
+    }
+    cudaError_t e = cudaGetLastError();
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaStreamDestroy(s);
+    cudaFree(out);
+    if (e != cudaSuccess)
+        return GJ_ERR_CUDA;
+    *tflops = 2.0 * 8.0 * iters * (double)grid * 256.0 / (best * 1e-3) / 1e12;
+    return GJ_OK;
+}
+
+}  // extern "C"

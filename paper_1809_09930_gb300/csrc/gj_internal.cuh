@@ -1,0 +1,143 @@
+// gj_internal.cuh -- shared declarations of the GB300 self-join library.
+//
+// Data kept in HBM by a built index (all device memory, library-owned):
+//   X        FP64 [d][npad]  points in cell order (sorted by linear cell id,
+//            then by the SORTIDU coordinate), dimensions in REORDER order,
+//            structure-of-arrays so a tile of candidates is d coalesced rows.
+//   orig     uint32 [n]      original row index of each sorted position.
+//   cell_start int64 [G+1]   first sorted position of each non-empty cell
+//            (Sec. 3.2.1: the "lookup array" ranges of the non-empty cells).
+//   cell_id  int64 [G]       linearised cell ids, ascending (Sec. 3.2.1).
+//   adj_start/adj            per cell, the non-empty adjacent cells b >= a
+//            (3^k search of Sec. 3.2.1, halved by symmetry).
+//   items    gj_item [nitems] query blocks of <= QB points of one cell.
+//   order    uint32 [nitems] items by descending estimated load.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/gj.h"
+
+namespace gj {
+
+constexpr int QB = 128;            // query block (points per work item)
+constexpr int MAXK = 8;            // most indexed dimensions
+
+struct Item {
+    uint32_t cell;   // query cell index
+    uint32_t qbeg;   // first sorted position of the block
+    uint32_t qlen;   // points in the block (<= QB)
+    uint32_t pad;
+};
+
+struct Deferred {    // resume point of an item whose results did not fit
+    uint32_t item;
+    uint32_t tile;   // first tile (in the item's tile order) not yet committed
+};
+
+// Device-side control block of one join launch.
+struct JoinCtl {
+    unsigned long long pos;        // pairs reserved in the output
+    unsigned long long fail_base;  // lowest base of a reservation that did not fit
+    unsigned long long counted;    // pairs counted (count-only launches)
+    unsigned long long survivors;  // tensor-core filter survivors
+    unsigned long long dims;       // dimensions evaluated (SHORTC depth summed over pairs)
+    unsigned long long evaluated;  // candidate pairs evaluated
+    unsigned int head;             // main-queue dequeue counter (monotone across launches)
+    unsigned int full;             // output filled during this launch
+    unsigned int din_head;         // deferred-in dequeue counter
+    unsigned int dout_n;           // deferred-out entries
+    unsigned int err;              // error bits (see kErr*)
+    unsigned int pad[3];
+};
+
+constexpr unsigned kErrStaging = 1u;   // a tile's output did not fit the staging area
+constexpr unsigned kErrTimeout = 2u;   // a bounded wait ran out
+constexpr unsigned kErrDeferred = 4u;  // deferred list overflow
+
+// Read-only geometry of an index, passed by value to kernels.
+struct IndexView {
+    const double *X;
+    const uint32_t *orig;
+    const int64_t *cell_start;
+    const int64_t *adj_start;
+    const uint32_t *adj;
+    const Item *items;
+    int64_t n, npad;
+    int d;
+    int u;          // SORTIDU dimension (reordered index), -1 = off
+    double e2;      // fl(eps*eps)
+    double ew;      // SORTIDU window half-width (eps widened)
+};
+
+struct JoinLaunch {
+    IndexView ix;
+    const uint32_t *queue;      // item ids in dequeue order
+    uint32_t qlimit;            // dequeue only while head < qlimit
+    const Deferred *din;        // resume points from the previous launch
+    uint32_t n_din;
+    Deferred *dout;
+    uint32_t dout_cap;
+    JoinCtl *ctl;
+    gj_pair *out;               // nullptr = count only
+    unsigned long long cap;
+    gj_pair *staging;           // per-CTA staging areas
+    uint32_t stg_cap;           // pairs per CTA
+};
+
+// ---- kernels and launchers (gj_index.cu) --------------------------------
+cudaError_t launch_check_finite(const double *P, int64_t count, unsigned int *flag, cudaStream_t s);
+cudaError_t launch_dim_stats(const double *P, int64_t n, int d, double *part, int nblk, double *stats,
+                             cudaStream_t s);
+
+struct Scratch;   // temporary device buffers of a build
+
+// radix sort of (key64, val32) pairs on bits [lo, hi); result in (k0, v0)
+cudaError_t radix_sort_pairs(uint64_t *k0, uint32_t *v0, uint64_t *k1, uint32_t *v1, int64_t n,
+                             int lo, int hi, uint32_t *counts, int64_t counts_cap, cudaStream_t s);
+
+// exclusive scan of int64 values in place; returns total via *total_dev (device)
+cudaError_t exclusive_scan_i64(int64_t *data, int64_t n, int64_t *tmp, int64_t tmp_cap,
+                               cudaStream_t s);
+
+int64_t radix_counts_needed(int64_t n);
+int64_t scan_tmp_needed(int64_t n);
+int build_index(gj_index *h, const double *P, int64_t n, int d, double eps, int k_req, uint32_t flags,
+                cudaStream_t s);
+
+// ---- join kernels (gj_join.cu) -------------------------------------------
+cudaError_t launch_join_plain(const JoinLaunch &L, int grid, cudaStream_t s);
+int plain_ctas_per_sm(int d);
+size_t plain_smem_bytes(int d);
+cudaError_t launch_fp64_probe(double *out, int iters, int grid, cudaStream_t s);
+
+}  // namespace gj
+
+// The handle (gj_api.cu)
+struct gj_index {
+    int device;
+    cudaStream_t stream;
+    bool own_stream;
+    cudaStream_t drain_stream;
+    gj_config cfg;
+    gj_index_info_t info;
+    gj_join_stats last;
+    // device arrays
+    double *X;
+    uint32_t *orig;
+    int64_t *cell_start;
+    int64_t *cell_id;
+    int64_t *adj_start;
+    uint32_t *adj;
+    gj::Item *items;
+    uint32_t *order;     // items by descending load
+    int64_t npad;
+    int64_t G;
+    int64_t nitems;
+    int u;
+    double e2, ew;
+    int sms;
+};

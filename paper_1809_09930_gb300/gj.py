@@ -1,0 +1,295 @@
+"""Python binding of the C ABI in include/gj.h (argument marshalling only).
+
+Every function here has the name of the C entry point it calls and does no
+arithmetic of the join: points go in as numpy arrays or torch tensors (host or
+CUDA), pairs come back in caller-provided or freshly allocated buffers.  The
+library must have been built (``__graft_entry__.build()`` or
+``python -m paper_1809_09930_gb300._build``); importing this module without it
+raises, there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libgj.so")
+
+GJ_OK = 0
+GJ_ERR_INVALID_ARG = -1
+GJ_ERR_NONFINITE = -2
+GJ_ERR_OOM = -3
+GJ_ERR_CUDA = -4
+GJ_ERR_CAPACITY = -5
+GJ_ERR_TIMEOUT = -6
+GJ_ERR_UNSUPPORTED = -7
+GJ_ERR_TOO_LARGE = -8
+GJ_MAX_DIMS = 1024
+
+GJ_REORDER = 1 << 0
+GJ_SORTIDU = 1 << 1
+GJ_SHORTC = 1 << 2
+GJ_TC_FILTER = 1 << 3
+GJ_DEFAULT_FLAGS = GJ_REORDER | GJ_SORTIDU | GJ_SHORTC
+
+
+class GJError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        super().__init__(f"{what}: {gj_status_string(status)} ({status})" if what else gj_status_string(status))
+
+
+class gj_config(C.Structure):
+    _fields_ = [("k", C.c_int32), ("flags", C.c_uint32), ("stream", C.c_void_p),
+                ("batch_pairs", C.c_uint64), ("device", C.c_int32), ("reserved", C.c_uint32 * 7)]
+
+
+class gj_index_info_t(C.Structure):
+    _fields_ = [("n", C.c_int64), ("d", C.c_int32), ("k", C.c_int32), ("eps", C.c_double),
+                ("nonempty_cells", C.c_int64), ("work_items", C.c_int64),
+                ("candidate_pairs", C.c_uint64), ("window_pairs", C.c_uint64),
+                ("flags", C.c_uint32), ("sortidu_dim", C.c_int32),
+                ("perm", C.c_int32 * GJ_MAX_DIMS)]
+
+
+class gj_join_stats(C.Structure):
+    _fields_ = [("pairs", C.c_uint64), ("launches", C.c_uint32), ("batches_planned", C.c_uint32),
+                ("batch_pairs", C.c_uint64), ("estimate", C.c_uint64), ("tc_survivors", C.c_uint64),
+                ("evaluated", C.c_uint64), ("dims", C.c_uint64), ("join_ms", C.c_double),
+                ("estimate_ms", C.c_double), ("total_ms", C.c_double)]
+
+
+EXPORTS = ["gj_config_init", "gj_index_build", "gj_index_build_ex", "gj_self_join",
+           "gj_self_join_part", "gj_index_get_info", "gj_last_join_stats", "gj_free",
+           "gj_last_status", "gj_status_string", "gj_version", "gj_probe_fp64_tflops"]
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load libgj.so and declare the C signatures."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise ImportError(f"the CUDA library {p} is not built; run __graft_entry__.build()")
+    lib = C.CDLL(p)
+    V = C.c_void_p
+    lib.gj_config_init.restype = None
+    lib.gj_config_init.argtypes = [C.POINTER(gj_config)]
+    lib.gj_index_build.restype = V
+    lib.gj_index_build.argtypes = [V, C.c_int64, C.c_int32, C.c_double, C.c_int32]
+    lib.gj_index_build_ex.restype = V
+    lib.gj_index_build_ex.argtypes = [V, C.c_int64, C.c_int32, C.c_double, C.POINTER(gj_config)]
+    lib.gj_self_join.restype = C.c_int
+    lib.gj_self_join.argtypes = [V, V, C.c_uint64, C.POINTER(C.c_uint64)]
+    lib.gj_self_join_part.restype = C.c_int
+    lib.gj_self_join_part.argtypes = [V, C.c_int32, C.c_int32, V, C.c_uint64, C.POINTER(C.c_uint64)]
+    lib.gj_index_get_info.restype = C.c_int
+    lib.gj_index_get_info.argtypes = [V, C.POINTER(gj_index_info_t)]
+    lib.gj_last_join_stats.restype = C.c_int
+    lib.gj_last_join_stats.argtypes = [V, C.POINTER(gj_join_stats)]
+    lib.gj_free.restype = None
+    lib.gj_free.argtypes = [V]
+    lib.gj_last_status.restype = C.c_int
+    lib.gj_last_status.argtypes = []
+    lib.gj_status_string.restype = C.c_char_p
+    lib.gj_status_string.argtypes = [C.c_int]
+    lib.gj_version.restype = C.c_char_p
+    lib.gj_version.argtypes = []
+    lib.gj_probe_fp64_tflops.restype = C.c_int
+    lib.gj_probe_fp64_tflops.argtypes = [C.c_int32, C.POINTER(C.c_double)]
+    if path is None:
+        _lib = lib
+    return lib
+
+
+# ---------------------------------------------------------------------------
+# marshalling helpers
+# ---------------------------------------------------------------------------
+
+def _ptr_points(points):
+    """(pointer, n, d, keepalive) for an (n, d) float64 array or tensor."""
+    try:
+        import torch
+        if isinstance(points, torch.Tensor):
+            if points.dtype != torch.float64 or points.dim() != 2:
+                raise TypeError("points must be a 2-D float64 tensor")
+            t = points.contiguous()
+            return t.data_ptr(), t.shape[0], t.shape[1], t
+    except ImportError:  # pragma: no cover
+        pass
+    a = np.ascontiguousarray(points, dtype=np.float64)
+    if a.ndim != 2:
+        raise TypeError("points must be a 2-D array")
+    return a.ctypes.data, a.shape[0], a.shape[1], a
+
+
+def _ptr_pairs(out):
+    """(pointer, capacity in pairs, keepalive) for a (cap, 2) uint32 buffer."""
+    if out is None:
+        return None, 0, None
+    try:
+        import torch
+        if isinstance(out, torch.Tensor):
+            if out.dtype not in (torch.int32, torch.uint32) or out.dim() != 2 or out.shape[1] != 2 \
+                    or not out.is_contiguous():
+                raise TypeError("pair buffer must be a contiguous (cap, 2) int32/uint32 tensor")
+            return out.data_ptr(), out.shape[0], out
+    except ImportError:  # pragma: no cover
+        pass
+    if not (isinstance(out, np.ndarray) and out.dtype == np.uint32 and out.ndim == 2
+            and out.shape[1] == 2 and out.flags.c_contiguous):
+        raise TypeError("pair buffer must be a C-contiguous (cap, 2) uint32 array")
+    return out.ctypes.data, out.shape[0], out
+
+
+# ---------------------------------------------------------------------------
+# the C entry points, by name
+# ---------------------------------------------------------------------------
+
+def gj_config_init() -> gj_config:
+    cfg = gj_config()
+    load().gj_config_init(C.byref(cfg))
+    return cfg
+
+
+def gj_index_build(points, eps: float, k: int = 0) -> int:
+    p, n, d, keep = _ptr_points(points)
+    h = load().gj_index_build(p, n, d, float(eps), int(k))
+    del keep
+    if not h:
+        raise GJError(gj_last_status(), "gj_index_build")
+    return h
+
+
+def gj_index_build_ex(points, eps: float, cfg: gj_config) -> int:
+    p, n, d, keep = _ptr_points(points)
+    h = load().gj_index_build_ex(p, n, d, float(eps), C.byref(cfg))
+    del keep
+    if not h:
+        raise GJError(gj_last_status(), "gj_index_build_ex")
+    return h
+
+
+def gj_self_join(h: int, out=None) -> tuple[int, int]:
+    """Returns (status, |R|); pairs land in ``out`` when it is large enough."""
+    p, cap, keep = _ptr_pairs(out)
+    cnt = C.c_uint64(0)
+    st = load().gj_self_join(h, p, cap, C.byref(cnt))
+    del keep
+    return st, int(cnt.value)
+
+
+def gj_self_join_part(h: int, part: int, nparts: int, out=None) -> tuple[int, int]:
+    p, cap, keep = _ptr_pairs(out)
+    cnt = C.c_uint64(0)
+    st = load().gj_self_join_part(h, int(part), int(nparts), p, cap, C.byref(cnt))
+    del keep
+    return st, int(cnt.value)
+
+
+def gj_index_get_info(h: int) -> dict:
+    info = gj_index_info_t()
+    st = load().gj_index_get_info(h, C.byref(info))
+    if st != GJ_OK:
+        raise GJError(st, "gj_index_get_info")
+    out = {f: getattr(info, f) for f, _ in gj_index_info_t._fields_ if f != "perm"}
+    out["perm"] = [int(info.perm[j]) for j in range(info.d)]
+    return out
+
+
+def gj_last_join_stats(h: int) -> dict:
+    st_ = gj_join_stats()
+    st = load().gj_last_join_stats(h, C.byref(st_))
+    if st != GJ_OK:
+        raise GJError(st, "gj_last_join_stats")
+    return {f: getattr(st_, f) for f, _ in gj_join_stats._fields_}
+
+
+def gj_free(h: int) -> None:
+    if h:
+        load().gj_free(h)
+
+
+def gj_last_status() -> int:
+    return int(load().gj_last_status())
+
+
+def gj_status_string(status: int) -> str:
+    return load().gj_status_string(int(status)).decode()
+
+
+def gj_version() -> str:
+    return load().gj_version().decode()
+
+
+def gj_probe_fp64_tflops(device: int = -1) -> float:
+    v = C.c_double(0.0)
+    st = load().gj_probe_fp64_tflops(int(device), C.byref(v))
+    if st != GJ_OK:
+        raise GJError(st, "gj_probe_fp64_tflops")
+    return float(v.value)
+
+
+# ---------------------------------------------------------------------------
+# convenience
+# ---------------------------------------------------------------------------
+
+class Index:
+    """Owns a gj_index handle."""
+
+    def __init__(self, points, eps: float, k: int = 0, flags: int = GJ_DEFAULT_FLAGS,
+                 stream=None, batch_pairs: int = 0, device: int = -1):
+        cfg = gj_config_init()
+        cfg.k = int(k)
+        cfg.flags = int(flags)
+        cfg.stream = int(stream) if stream else None
+        cfg.batch_pairs = int(batch_pairs)
+        cfg.device = int(device)
+        self.h = gj_index_build_ex(points, eps, cfg)
+
+    def close(self):
+        if self.h:
+            gj_free(self.h)
+            self.h = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def info(self) -> dict:
+        return gj_index_get_info(self.h)
+
+    def stats(self) -> dict:
+        return gj_last_join_stats(self.h)
+
+    def count(self) -> int:
+        st, n = gj_self_join(self.h, None)
+        if st != GJ_OK:
+            raise GJError(st, "gj_self_join (count)")
+        return n
+
+    def join(self, out=None, part: int | None = None, nparts: int = 1):
+        """Pairs as a (|R|, 2) uint32 numpy array (or the given buffer's prefix)."""
+        if out is None:
+            n = self.count() if part is None else gj_self_join_part(self.h, part, nparts, None)[1]
+            out = np.empty((max(n, 1), 2), dtype=np.uint32)
+        if part is None:
+            st, n = gj_self_join(self.h, out)
+        else:
+            st, n = gj_self_join_part(self.h, part, nparts, out)
+        if st != GJ_OK:
+            raise GJError(st, "gj_self_join")
+        return out[:n]

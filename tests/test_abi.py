@@ -1,0 +1,68 @@
+"""The C-ABI library builds, loads and exports every function include/gj.h declares
+(no GPU needed: nothing here launches a kernel)."""
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "gj.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"\b(gj_[a-z0-9_]+)\s*\(", src)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1809_09930_gb300 import _build
+    _build.build()
+    from paper_1809_09930_gb300 import gj
+    return gj.load()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ("gj_index_build", "gj_self_join", "gj_free", "gj_last_status", "gj_status_string"):
+        assert must in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_1809_09930_gb300 import gj
+    so = gj.LIB_PATH
+    out = subprocess.run(["nm", "-D", "--defined-only", so], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\b(gj_[a-z0-9_]+)\b", out))
+    missing = [f for f in declared_functions() if f not in exported]
+    assert not missing, f"declared but not exported: {missing}"
+    for f in declared_functions():
+        assert hasattr(lib, f)
+    assert set(gj.EXPORTS) == set(declared_functions())
+
+
+def test_host_only_entry_points(lib):
+    from paper_1809_09930_gb300 import gj
+    assert gj.gj_version().count(".") == 2
+    assert gj.gj_status_string(gj.GJ_ERR_CAPACITY).startswith("result larger")
+    cfg = gj.gj_config_init()
+    assert cfg.flags == gj.GJ_DEFAULT_FLAGS and cfg.k == 0 and cfg.device == -1
+    lib.gj_free(None)   # NULL-safe
+
+
+def test_no_gpu_build_fails_loudly(lib):
+    """Without a usable GPU the build reports GJ_ERR_UNSUPPORTED; it never falls
+    back to a CPU path."""
+    import numpy as np
+    try:
+        import torch
+        if torch.cuda.is_available():
+            pytest.skip("a GPU is present")
+    except ImportError:
+        pass
+    from paper_1809_09930_gb300 import gj
+    with pytest.raises(gj.GJError) as e:
+        gj.Index(np.zeros((4, 2)), 0.5)
+    assert e.value.status == gj.GJ_ERR_UNSUPPORTED
