@@ -1,0 +1,371 @@
+"""Benchmark of the GB300 ε-distance self-join (one JSON line on rank 0).
+
+Workload: the paper-scale synthetic configuration -- 2,000,000 points i.i.d.
+uniform in [0,1)^d, FP64, ε per d chosen (by the CPU oracle, offline) for 32
+mean neighbours, k chosen automatically.  A step runs the whole hot path on
+each listed d: REORDER, grid index, adjacent-cell search, SHORTC distances (or
+the tensor-core filter + FP64 recheck) and result emission into a device
+buffer.  Metric: distance evaluations per second, where one evaluation is one
+unordered candidate pair of the paper's grid at the chosen k (points in
+adjacent cells, i < j; here the grid holds every pair), the unit fixed by the
+index and independent of the kernels.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--form plain|tc]
+                  [--dims 16,32,64] [--impl ours|reference]
+
+--impl reference times the CPU oracle (test infrastructure, plain C) on a
+bounded sample of the same workload.  Under torchrun each rank joins the
+entity partition (Sec. 6.2) part=rank of N (no data-path collective; only the
+timing max and the counts are reduced).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+WORKLOADS = os.path.join(ROOT, "tests", "golden", "workloads.json")
+PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=None)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--form", choices=["plain", "tc"], default="plain")
+    ap.add_argument("--dims", default=None, help="comma list of d for the paper-scale workload")
+    ap.add_argument("--n", type=int, default=2_000_000)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-baseline", action="store_true", help="skip the CPU oracle leg")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self) -> dict | None:
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.t:
+            self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1].split()[0]))
+                smax.append(float(f[2].split()[0]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+
+def workload(args):
+    with open(WORKLOADS) as f:
+        W = json.load(f)
+    dims = [int(x) for x in (args.dims or ("16,32,64" if args.form == "tc" else "16")).split(",")]
+    runs = []
+    for d in dims:
+        w = W[f"paper_d{d}"]
+        runs.append(dict(d=d, n=args.n, eps=w["eps"], seed=w["seed"],
+                         depth=w.get("depth_per_pair")))
+    return runs
+
+
+def cpu_baseline(runs, budget_s=15.0):
+    """The oracle, as it stands, on a bounded sample: the first m points of each
+    run's point set, m sized for ~budget_s of CPU work in total."""
+    import oracle
+    cores = os.cpu_count() or 1
+    evals, secs, parts = 0, 0.0, []
+    per = budget_s / len(runs)
+    for r in runs:
+        m = 8000
+        while True:
+            X = synth.uniform(m, r["d"], r["seed"])
+            t = time.perf_counter()
+            st = oracle.grid_count(X, r["eps"], k=1)
+            dt = time.perf_counter() - t
+            if dt > per * 0.3 or m >= r["n"]:
+                break
+            m = min(r["n"], int(m * math.sqrt(per / max(dt, 1e-3)) * 0.9))
+        evals += st["candidates"]
+        secs += dt
+        parts.append(f"first {m} points of the d={r['d']} set")
+    return {"value": evals / secs, "unit": "distance evals/s", "cores": cores, "kind": "oracle",
+            "sample": "; ".join(parts) + f"; {secs:.1f} s of CPU work"}
+
+
+def reference_arm(args, runs):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    steps = args.steps if args.steps is not None else 2
+    import oracle
+    oracle.build()
+    cb = None
+    vals = []
+    for _ in range(args.warmup + steps):
+        cb = cpu_baseline(runs, budget_s=20.0)
+        vals.append(cb["value"])
+    v = statistics.median(vals[args.warmup:]) if steps else vals[-1]
+    out = {"metric": "distance evals/s (self-join, exact pair set)", "value": v,
+           "unit": "distance evals/s", "n_gpus": args.gpus, "steps": steps, "warmup": args.warmup,
+           "ms_per_step": None, "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
+           "dtype": "f64", "data": "synthetic", "impl": "reference",
+           "config": {"workload": f"paper-scale uniform, n={args.n}, d in {[r['d'] for r in runs]}",
+                      "form": "cpu-oracle", "sample": cb["sample"]},
+           "cpu_baseline": dict(cb, value=v),
+           "e2e": {"value": v, "unit": "distance evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    runs = workload(args)
+    if args.impl == "reference":
+        reference_arm(args, runs)
+        return
+
+    import torch
+    from paper_1809_09930_gb300 import gj
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    steps = args.steps if args.steps is not None else (1 if args.form == "plain" else 5)
+    flags = gj.GJ_DEFAULT_FLAGS | (gj.GJ_TC_FILTER if args.form == "tc" else 0)
+    stream = torch.cuda.current_stream()
+
+    # inputs resident in HBM before the timed region; outputs to a device buffer
+    data = []
+    for r in runs:
+        X = synth.uniform(r["n"], r["d"], r["seed"])
+        Xd = torch.from_numpy(X).to("cuda")
+        data.append((r, X, Xd))
+    torch.cuda.synchronize()
+
+    def one_step(collect):
+        tot_evals = 0
+        for r, X, Xd in data:
+            ix = gj.Index(Xd, r["eps"], k=0, flags=flags, stream=stream.cuda_stream)
+            info = ix.info()
+            cap = collect["cap"].get(r["d"])
+            if cap is None:
+                cnt = ix.count()
+                cap = int(cnt * 1.02) + 1024
+                collect["cap"][r["d"]] = cap
+                collect["out"][r["d"]] = torch.empty((cap, 2), dtype=torch.int32, device="cuda")
+            st, cnt = gj.gj_self_join_part(ix.h, rank, world, collect["out"][r["d"]])
+            if st != gj.GJ_OK:
+                raise RuntimeError(f"join failed: {gj.gj_status_string(st)}")
+            s = ix.stats()
+            collect["join_ms"] += s["join_ms"]
+            collect["launches_join"] += s["launches"]
+            collect["dims"] += s["dims"]
+            collect["evaluated"] += s["evaluated"]
+            collect["pairs"][r["d"]] = cnt
+            collect["k"][r["d"]] = info["k"]
+            collect["flops"] += 2.0 * r["d"] * info["candidate_pairs"] / world
+            collect["survivors"] += s["tc_survivors"]
+            tot_evals += info["candidate_pairs"]
+            ix.close()
+        return tot_evals
+
+    def fresh():
+        return {"cap": {}, "out": {}, "join_ms": 0.0, "launches_join": 0, "dims": 0, "evaluated": 0,
+                "pairs": {}, "k": {}, "flops": 0.0, "survivors": 0}
+
+    col = fresh()
+    for _ in range(args.warmup):
+        one_step(col)
+    fp64_tflops = gj.gj_probe_fp64_tflops()
+
+    keep = {"cap": col["cap"], "out": col["out"]}
+    col = fresh()
+    col.update(keep)
+    clocks = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    l0 = gj.gj_kernel_launches()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    evals = 0
+    for _ in range(steps):
+        evals += one_step(col)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    launches = gj.gj_kernel_launches() - l0
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    # evals: the whole job's candidate pairs (parts of one join sum to the join)
+    value = evals / (ms * 1e-3)
+
+    # roofline of the dominant kernel (the join), from its own CUDA-event time
+    join_s = col["join_ms"] * 1e-3
+    if args.form == "plain":
+        # FP64 pipe: 2 instructions (DADD, DFMA) = 3 FLOPs per evaluated dimension;
+        # the mix's ceiling is 3/4 of the FMA-only rate the probe measures.
+        achieved = 3.0 * col["dims"] / join_s / 1e12
+        peak = 0.75 * fp64_tflops
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": "k_join_plain", "peak_source": "FP64 FMA probe measured in this run x 3/4 "
+                "(DADD+DFMA mix)", "fp64_fma_tflops_measured": fp64_tflops}
+    else:
+        # contraction work: 2*d FLOPs per unordered candidate pair (the dot
+        # product a.b; norms and padding excluded) over the join kernels' time
+        with open(PEAKS) as f:
+            pk = json.load(f)
+        peak = pk.get("bf16_tflops_sustained") or pk.get("bf16_tflops")
+        achieved = col["flops"] / join_s / 1e12
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None, "kernel": "k_join_tc",
+                "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (fp16 runs at the bf16 rate)",
+                "survivors_per_step": col["survivors"] / steps}
+
+    # end to end through the C ABI with host buffers (pinned), copies inside
+    e2e = None
+    if not args.no_e2e:
+        hin = [torch.from_numpy(X).pin_memory() for _, X, _ in data]
+        hout = {r["d"]: torch.empty((col["cap"][r["d"]], 2), dtype=torch.int32).pin_memory()
+                for r, _, _ in data}
+        def e2e_step():
+            ev = 0
+            for (r, X, _), hx in zip(data, hin):
+                ix = gj.Index(hx, r["eps"], k=0, flags=flags)
+                info = ix.info()
+                st, cnt = gj.gj_self_join_part(ix.h, rank, world, hout[r["d"]])
+                if st != gj.GJ_OK:
+                    raise RuntimeError(gj.gj_status_string(st))
+                ev += info["candidate_pairs"]
+                ix.close()
+            return ev
+        e2e_step()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ev = 0
+        for _ in range(steps):
+            ev += e2e_step()
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([e2e_s], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        h2d = sum(X.nbytes for _, X, _ in data)
+        d2h = sum(8 * col["pairs"][r["d"]] for r, _, _ in data)
+        e2e = {"value": ev / e2e_s, "unit": "distance evals/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h}
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    cb = None if (args.no_baseline or world > 1) else cpu_baseline(runs)
+    out = {
+        "metric": "distance evals/s (self-join, exact pair set)",
+        "value": value,
+        "unit": "distance evals/s",
+        "n_gpus": world,
+        "steps": steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms / steps,
+        "higher_is_better": True,
+        "scaling": "strong",
+        "vs_baseline": None,
+        "dtype": "f64" if args.form == "plain" else "f16xf16->f32 filter + f64 recheck",
+        "data": "synthetic",
+        "config": {"workload": f"paper-scale uniform [0,1)^d, n={args.n}, d in {[r['d'] for r in runs]}, "
+                               f"eps for 32 mean neighbours",
+                   "form": args.form, "eps": {r["d"]: r["eps"] for r in runs}, "k": col["k"],
+                   "pairs": col["pairs"], "parallelism": f"entity partition x{world}",
+                   "l2": "inputs larger than L2 (>=256 MB per point set)",
+                   "step": "index build (REORDER, grid, adjacency, queue) + join into a device buffer"},
+        "roofline": roof,
+        "cpu_baseline": cb,
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "join_stats": {"join_ms_total": col["join_ms"], "join_launches": col["launches_join"],
+                       "dims_evaluated": col["dims"], "pairs_evaluated": col["evaluated"]},
+    }
+    print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -179,6 +179,17 @@ const char *gj_version(void);
  * roofline.  device = -1 for the current device. */
 int gj_probe_fp64_tflops(int32_t device, double *tflops);
 
+/* Diagnostic (no paper counterpart): one 128 x 128 tile D = A * B^T on the
+ * tensor cores through the operand layout, descriptors and TMEM path of the
+ * GJ_TC_FILTER join.  A and B are row-major [128][Kp] fp16 bit patterns in host
+ * memory, Kp a multiple of 16 in [16, 128]; D is row-major [128][128] fp32 in
+ * host memory.  Runs on the current device; returns GJ_OK or an error code. */
+int gj_debug_tc_tile(const uint16_t *A, const uint16_t *B, int32_t Kp, float *D);
+
+/* Measurement helper (no paper counterpart): number of CUDA kernels this
+ * library has launched in this process so far (all handles, all threads). */
+unsigned long long gj_kernel_launches(void);
+
 #ifdef __cplusplus
 }
 #endif

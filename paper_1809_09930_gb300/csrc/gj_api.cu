@@ -18,6 +18,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <vector>
 
@@ -26,6 +27,12 @@
 using namespace gj;
 
 static thread_local int t_last_status = GJ_OK;
+static std::atomic<unsigned long long> g_launches{0};
+
+namespace gj {
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+unsigned long long launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
+}  // namespace gj
 
 namespace {
 
@@ -136,7 +143,7 @@ int run_launch(gj_index *h, JoinBuffers &B, JoinLaunch L, int grid, JoinCtl init
         return cuda_status(e);
     L.ctl = B.ctl;
     cudaEventRecord(B.ev_k0, s);
-    e = launch_join_plain(L, grid, s);
+    e = h->tc_ready ? launch_join_tc(h, L, grid, s) : launch_join_plain(L, grid, s);
     if (e != cudaSuccess)
         return cuda_status(e);
     cudaEventRecord(B.ev_k1, s);
@@ -175,11 +182,13 @@ int join_impl(gj_index *h, int part, int nparts, gj_pair *pairs_out, uint64_t ca
         h->last.total_ms = now_ms() - t_start;
         return GJ_OK;
     }
-    const int per_sm = plain_ctas_per_sm(h->info.d);
+    const int per_sm = h->tc_ready ? 1 : plain_ctas_per_sm(h->info.d);
     if (per_sm < 1)
         return GJ_ERR_UNSUPPORTED;
     const int grid = h->sms * per_sm;
-    const uint32_t stg_cap = 1u << 16;   // pairs per CTA staging area (>= 4 tiles of output)
+    // pairs per CTA staging area: plain >= 4 tiles of output; tensor-core: two halves
+    const uint32_t stg_cap = 1u << 16;
+    const size_t stg_per_cta = h->tc_ready ? tc_staging_pairs_per_cta() : (size_t)stg_cap;
     const bool dev_out = is_device_ptr(pairs_out);
     const bool count_only_call = (cap == 0);
 
@@ -193,8 +202,10 @@ int join_impl(gj_index *h, int part, int nparts, gj_pair *pairs_out, uint64_t ca
     TRYC(cudaMalloc(&B.ctl, sizeof(JoinCtl)));
     TRYC(cudaMallocHost(&B.hctl_up, sizeof(JoinCtl)));
     TRYC(cudaMallocHost(&B.hctl_dn, sizeof(JoinCtl)));
-    TRYC(cudaMalloc(&B.def[0], (size_t)grid * sizeof(Deferred)));
-    TRYC(cudaMalloc(&B.def[1], (size_t)grid * sizeof(Deferred)));
+    // a CTA defers at most the items in its pipeline when the output fills
+    const uint32_t dcap = (uint32_t)grid * 8u;
+    TRYC(cudaMalloc(&B.def[0], (size_t)dcap * sizeof(Deferred)));
+    TRYC(cudaMalloc(&B.def[1], (size_t)dcap * sizeof(Deferred)));
     TRYC(cudaMalloc(&B.queue, nq * sizeof(uint32_t)));
     TRYC(cudaMalloc(&B.qtmp, nq * sizeof(uint32_t)));
     TRYC(cudaEventCreate(&B.ev_k0));
@@ -205,13 +216,14 @@ int join_impl(gj_index *h, int part, int nparts, gj_pair *pairs_out, uint64_t ca
 
     JoinLaunch L{};
     L.ix = view_of(h);
-    L.dout_cap = (uint32_t)grid;
+    L.dout_cap = dcap;
     L.stg_cap = stg_cap;
     double kms = 0.0;
     uint32_t launches = 0;
-    unsigned long long evaluated = 0, dims = 0;
+    unsigned long long evaluated = 0, dims = 0, survivors = 0;
 
     // ---- 1. sampled estimate of |R| (count-only over every S-th item), Sec. 3.2.2
+    note_launch();
     k_gather_queue<<<(int)((nq + 255) / 256), 256, 0, s>>>(h->order, part, nparts, nq, 1, B.qtmp);
     TRYC(cudaGetLastError());
     uint64_t estimate = 0;
@@ -220,6 +232,7 @@ int join_impl(gj_index *h, int part, int nparts, gj_pair *pairs_out, uint64_t ca
     if (want_batches && h->cfg.batch_pairs == 0 && S >= 8) {
         const int64_t ns = (nq + S - 1) / S;
         TRYC(cudaMalloc(&B.sample, ns * sizeof(uint32_t)));
+        note_launch();
         k_stride_queue<<<(int)((ns + 255) / 256), 256, 0, s>>>(B.qtmp, nq, S, B.sample, ns);
         TRYC(cudaGetLastError());
         JoinLaunch Ls = L;
@@ -262,6 +275,7 @@ int join_impl(gj_index *h, int part, int nparts, gj_pair *pairs_out, uint64_t ca
     h->last.batch_pairs = want_batches ? bs : 0;
 
     // the dequeue order: nb interleaved ranges of the load order
+    note_launch();
     k_gather_queue<<<(int)((nq + 255) / 256), 256, 0, s>>>(h->order, part, nparts, nq, nb, B.queue);
     TRYC(cudaGetLastError());
     const int64_t qn = nq / nb, rem = nq % nb;
@@ -272,7 +286,7 @@ int join_impl(gj_index *h, int part, int nparts, gj_pair *pairs_out, uint64_t ca
         TRYC(cudaMalloc(&B.dbuf[1], bs * sizeof(gj_pair)));
     }
     if (!count_only_call)
-        TRYC(cudaMalloc(&B.staging, (size_t)grid * stg_cap * sizeof(gj_pair)));
+        TRYC(cudaMalloc(&B.staging, (size_t)grid * stg_per_cta * sizeof(gj_pair)));
 
     // ---- 3. batch loop
     uint64_t written = 0, total = 0;
@@ -320,6 +334,7 @@ int join_impl(gj_index *h, int part, int nparts, gj_pair *pairs_out, uint64_t ca
         ++launches;
         evaluated += res.evaluated;
         dims += res.dims;
+        survivors += res.survivors;
         if (counting) {
             total += res.counted;
         } else {
@@ -346,7 +361,7 @@ int join_impl(gj_index *h, int part, int nparts, gj_pair *pairs_out, uint64_t ca
                     counting = true;
             }
         }
-        n_din = std::min<uint32_t>(res.dout_n, (uint32_t)grid);
+        n_din = std::min<uint32_t>(res.dout_n, dcap);
         cur ^= 1;
         head = std::min<uint32_t>(res.head, qlimit);
         if (head >= qlimit && batch + 1 < nb)
@@ -361,7 +376,7 @@ int join_impl(gj_index *h, int part, int nparts, gj_pair *pairs_out, uint64_t ca
     h->last.launches = launches;
     h->last.join_ms = kms;
     h->last.total_ms = now_ms() - t_start;
-    h->last.tc_survivors = 0;
+    h->last.tc_survivors = survivors;
     h->last.evaluated = evaluated;
     h->last.dims = dims;
     if (st != GJ_OK)
@@ -552,6 +567,8 @@ void gj_free(gj_index *h)
     cudaFree(h->adj);
     cudaFree(h->items);
     cudaFree(h->order);
+    cudaFree(h->XA);
+    cudaFree(h->XB);
     if (h->drain_stream)
         cudaStreamDestroy(h->drain_stream);
     if (h->own_stream && h->stream)
@@ -578,6 +595,8 @@ const char *gj_status_string(int status)
 }
 
 const char *gj_version(void) { return "0.1.0"; }
+
+unsigned long long gj_kernel_launches(void) { return launches_so_far(); }
 
 int gj_probe_fp64_tflops(int device, double *tflops)
 {

@@ -53,6 +53,7 @@ cudaError_t launch_check_finite(const double *P, int64_t count, unsigned int *fl
     int64_t blocks = (count + 255) / 256;
     if (blocks > 4096)
         blocks = 4096;
+    note_launch();
     k_check_finite<<<(int)blocks, 256, 0, s>>>(P, count, flag);
     return cudaGetLastError();
 }
@@ -147,7 +148,9 @@ cudaError_t launch_dim_stats(const double *P, int64_t n, int d, double *part, in
             if (e != cudaSuccess)
                 return e;
         }
+        note_launch();
         k_dim_partial<<<nblk, 256, 0, s>>>(P, n, d, rows, pass, mean_col, part);
+        note_launch();
         k_dim_final<<<(d + 127) / 128, 128, 0, s>>>(part, nblk, d, n, pass, stats);
     }
     return cudaGetLastError();
@@ -347,8 +350,11 @@ cudaError_t radix_sort_pairs(uint64_t *k0, uint32_t *v0, uint64_t *k1, uint32_t 
     uint32_t *va = v0, *vb = v1;
     int passes = 0;
     for (int shift = lo; shift < hi; shift += 8) {
+        note_launch();
         k_rs_count<<<nblocks, RS_THREADS, 0, s>>>(ka, n, shift, counts, nblocks);
+        note_launch();
         k_rs_scan<<<256, 1024, 0, s>>>(counts, nblocks);
+        note_launch();
         k_rs_scatter<<<nblocks, RS_THREADS, 0, s>>>(ka, va, kb, vb, n, shift, counts, nblocks);
         uint64_t *tk = ka; ka = kb; kb = tk;
         uint32_t *tv = va; va = vb; vb = tv;
@@ -422,15 +428,18 @@ cudaError_t exclusive_scan_i64(int64_t *data, int64_t n, int64_t *tmp, int64_t t
         return cudaSuccess;
     int64_t nb = (n + SC_TILE - 1) / SC_TILE;
     if (nb == 1) {
+        note_launch();
         k_scan_block<<<1, SC_THREADS, 0, s>>>(data, n, nullptr);
         return cudaGetLastError();
     }
     if (tmp_cap < nb + 1)
         return cudaErrorInvalidValue;
+    note_launch();
     k_scan_block<<<(int)nb, SC_THREADS, 0, s>>>(data, n, tmp);
     cudaError_t e = exclusive_scan_i64(tmp, nb, tmp + nb + 1, tmp_cap - nb - 1, s);
     if (e != cudaSuccess)
         return e;
+    note_launch();
     k_scan_add<<<(int)nb, SC_THREADS, 0, s>>>(data, n, tmp);
     return cudaGetLastError();
 }
@@ -573,16 +582,16 @@ __global__ void k_adjacent(const int64_t *__restrict__ cell_id, const int64_t *_
 // ---------------------------------------------------------------------------
 // Work items
 // ---------------------------------------------------------------------------
-__global__ void k_item_counts(const int64_t *__restrict__ cell_start, int64_t G, int64_t *__restrict__ cnt)
+__global__ void k_item_counts(const int64_t *__restrict__ cell_start, int64_t G, int qb, int64_t *__restrict__ cnt)
 {
     int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (c < G)
-        cnt[c] = (cell_start[c + 1] - cell_start[c] + QB - 1) / QB;
+        cnt[c] = (cell_start[c + 1] - cell_start[c] + qb - 1) / qb;
 }
 
 // items of cell c at [istart[c], ...); cost key = ~float bits of the load
 // estimate (ascending key = descending load); also sums candidate pairs.
-__global__ void k_items(const int64_t *__restrict__ cell_start, int64_t G,
+__global__ void k_items(const int64_t *__restrict__ cell_start, int64_t G, int qb,
                         const int64_t *__restrict__ istart, const int64_t *__restrict__ nbsum,
                         Item *__restrict__ items, uint64_t *__restrict__ key, uint32_t *__restrict__ val,
                         unsigned long long *__restrict__ cand)
@@ -593,8 +602,8 @@ __global__ void k_items(const int64_t *__restrict__ cell_start, int64_t G,
     const int64_t s = cell_start[c], e = cell_start[c + 1], len = e - s;
     const int64_t nb = nbsum[c];
     int64_t it = istart[c];
-    for (int64_t q = s; q < e; q += QB, ++it) {
-        uint32_t ql = (uint32_t)min((int64_t)QB, e - q);
+    for (int64_t q = s; q < e; q += qb, ++it) {
+        uint32_t ql = (uint32_t)min((int64_t)qb, e - q);
         items[it] = Item{(uint32_t)c, (uint32_t)q, ql, 0u};
         float load = (float)ql * (float)(nb + (e - q));
         key[it] = (uint64_t)(~__float_as_uint(load));
@@ -706,8 +715,11 @@ int build_index(gj_index *h, const double *P, int64_t n, int d, double eps, int 
             if (nc_all[j] == 1)
                 invw_all[j] = 0.0;
         }
+        const bool tc = (flags & GJ_TC_FILTER) && ((d + 4 + 15) / 16) * 16 <= 128;
+        h->qb = tc ? QB_TC : QB_PLAIN;
         int kmax = std::min(d, MAXK);
-        k = (k_req > 0) ? std::min(k_req, kmax) : choose_k(d, nc_all, n, kmax);
+        // the tensor-core filter wants large cells (full 128 x 128 tiles): index at most 3 dims
+        k = (k_req > 0) ? std::min(k_req, kmax) : choose_k(d, nc_all, n, tc ? std::min(kmax, 3) : kmax);
         // cap k so the linear id fits in 62 bits
         while (k > 0) {
             long double prod = 1.0L;
@@ -756,14 +768,17 @@ int build_index(gj_index *h, const double *P, int64_t n, int d, double eps, int 
         if (n > 0) {
             const uint32_t *vin = nullptr;
             if (h->u >= 0) {
+                note_launch();
                 k_ukeys<<<(int)grid_blocks(n, 256), 256, 0, s>>>(P, n, d, perm[h->u], k0, v0);
                 GJ_TRY(cudaGetLastError());
                 GJ_TRY(radix_sort_pairs(k0, v0, k1, v1, n, 0, 64, counts, counts_cap, s));
                 // v0 = point ids ordered by u; cell keys in that order (v1 gets a copy)
                 GJ_TRY(cudaMemcpyAsync(v1, v0, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
                 vin = v1;
+                note_launch();
                 k_cellkeys<<<(int)grid_blocks(n, 256), 256, 0, s>>>(P, n, gp, vin, k0, nullptr);
             } else {
+                note_launch();
                 k_cellkeys<<<(int)grid_blocks(n, 256), 256, 0, s>>>(P, n, gp, nullptr, k0, v0);
             }
             GJ_TRY(cudaGetLastError());
@@ -775,6 +790,7 @@ int build_index(gj_index *h, const double *P, int64_t n, int d, double eps, int 
         GJ_TRY(cudaMalloc(&h->orig, maxn * sizeof(uint32_t)));
         GJ_TRY(cudaMemsetAsync(h->X, 0, (size_t)d * h->npad * sizeof(double), s));
         if (n > 0) {
+            note_launch();
             k_gather_soa<<<(int)grid_blocks(n, 32), 256, 0, s>>>(P, n, d, h->npad, v0, perm_dev, h->X, h->orig);
             GJ_TRY(cudaGetLastError());
         }
@@ -784,6 +800,7 @@ int build_index(gj_index *h, const double *P, int64_t n, int d, double eps, int 
         GJ_TRY(cudaMalloc(&tmp, tmp_cap * sizeof(int64_t)));
         GJ_TRY(cudaMalloc(&flagbuf, (maxn + 1) * sizeof(int64_t)));
         if (n > 0) {
+            note_launch();
             k_heads<<<(int)grid_blocks(n, 256), 256, 0, s>>>(k0, n, flagbuf);
             int64_t last_flag = 0;
             GJ_TRY(cudaMemcpyAsync(&last_flag, flagbuf + n - 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
@@ -797,10 +814,13 @@ int build_index(gj_index *h, const double *P, int64_t n, int d, double eps, int 
         GJ_TRY(cudaMalloc(&h->cell_start, (G + 1) * sizeof(int64_t)));
         GJ_TRY(cudaMalloc(&h->cell_id, std::max<int64_t>(G, 1) * sizeof(int64_t)));
         if (n > 0) {
+            note_launch();
             k_cells<<<(int)grid_blocks(n, 256), 256, 0, s>>>(k0, n, flagbuf, h->cell_start, h->cell_id);
+            note_launch();
             k_set_i64<<<1, 1, 0, s>>>(h->cell_start + G, n);
             GJ_TRY(cudaGetLastError());
         } else {
+            note_launch();
             k_set_i64<<<1, 1, 0, s>>>(h->cell_start, 0);
         }
 
@@ -810,6 +830,7 @@ int build_index(gj_index *h, const double *P, int64_t n, int d, double eps, int 
         GJ_TRY(cudaMalloc(&h->adj_start, (G + 1) * sizeof(int64_t)));
         if (G > 0) {
             int64_t thr = G * 32;
+            note_launch();
             k_adjacent<<<(int)grid_blocks(thr, 256), 256, 0, s>>>(h->cell_id, h->cell_start, G, ap, 0, cnt,
                                                                   nbsum, nullptr, nullptr);
             GJ_TRY(cudaGetLastError());
@@ -820,12 +841,15 @@ int build_index(gj_index *h, const double *P, int64_t n, int d, double eps, int 
             GJ_TRY(cudaMemcpyAsync(&last_pre, h->adj_start + G - 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
             GJ_TRY(cudaStreamSynchronize(s));
             nadj = last_pre + last_cnt;
+            note_launch();
             k_set_i64<<<1, 1, 0, s>>>(h->adj_start + G, nadj);
             GJ_TRY(cudaMalloc(&h->adj, std::max<int64_t>(nadj, 1) * sizeof(uint32_t)));
+            note_launch();
             k_adjacent<<<(int)grid_blocks(thr, 256), 256, 0, s>>>(h->cell_id, h->cell_start, G, ap, 1, nullptr,
                                                                   nullptr, h->adj_start, h->adj);
             GJ_TRY(cudaGetLastError());
         } else {
+            note_launch();
             k_set_i64<<<1, 1, 0, s>>>(h->adj_start, 0);
             GJ_TRY(cudaMalloc(&h->adj, sizeof(uint32_t)));
         }
@@ -834,7 +858,8 @@ int build_index(gj_index *h, const double *P, int64_t n, int d, double eps, int 
         GJ_TRY(cudaMalloc(&cand_dev, sizeof(unsigned long long)));
         GJ_TRY(cudaMemsetAsync(cand_dev, 0, sizeof(unsigned long long), s));
         if (G > 0) {
-            k_item_counts<<<(int)grid_blocks(G, 256), 256, 0, s>>>(h->cell_start, G, cnt);
+            note_launch();
+            k_item_counts<<<(int)grid_blocks(G, 256), 256, 0, s>>>(h->cell_start, G, h->qb, cnt);
             int64_t last_cnt = 0, last_pre = 0;
             GJ_TRY(cudaMemcpyAsync(&last_cnt, cnt + G - 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
             GJ_TRY(exclusive_scan_i64(cnt, G, tmp, tmp_cap, s));
@@ -850,7 +875,8 @@ int build_index(gj_index *h, const double *P, int64_t n, int d, double eps, int 
                 st = GJ_ERR_CUDA;
                 goto done;
             }
-            k_items<<<(int)grid_blocks(G, 256), 256, 0, s>>>(h->cell_start, G, cnt, nbsum, h->items, k0, v0,
+            note_launch();
+            k_items<<<(int)grid_blocks(G, 256), 256, 0, s>>>(h->cell_start, G, h->qb, cnt, nbsum, h->items, k0, v0,
                                                              cand_dev);
             GJ_TRY(cudaGetLastError());
             GJ_TRY(radix_sort_pairs(k0, v0, k1, v1, nitems, 0, 32, counts, counts_cap, s));
@@ -860,6 +886,11 @@ int build_index(gj_index *h, const double *P, int64_t n, int d, double eps, int 
         GJ_TRY(cudaMemcpyAsync(&cand, cand_dev, sizeof(cand), cudaMemcpyDeviceToHost, s));
         GJ_TRY(cudaStreamSynchronize(s));
         h->info.candidate_pairs = cand;
+        if ((flags & GJ_TC_FILTER) && n > 0) {
+            st = tc_prepare(h, hs.data(), perm.data(), s);
+            if (st != GJ_OK)
+                goto done;
+        }
     }
     h->info.nonempty_cells = G;
     h->info.work_items = nitems;

@@ -23,7 +23,9 @@
 
 namespace gj {
 
-constexpr int QB = 128;            // query block (points per work item)
+constexpr int QB = 128;            // most points of a work item the plain kernel holds
+constexpr int QB_PLAIN = 120;      // query block of a plain-path index
+constexpr int QB_TC = 248;         // query block of a tensor-core index (256-row A tile from qbeg & ~7)
 constexpr int MAXK = 8;            // most indexed dimensions
 
 struct Item {
@@ -88,6 +90,11 @@ struct JoinLaunch {
     uint32_t stg_cap;           // pairs per CTA
 };
 
+// Count of kernels this library has launched (process-wide); read through
+// gj_kernel_launches().
+void note_launch();
+unsigned long long launches_so_far();
+
 // ---- kernels and launchers (gj_index.cu) --------------------------------
 cudaError_t launch_check_finite(const double *P, int64_t count, unsigned int *flag, cudaStream_t s);
 cudaError_t launch_dim_stats(const double *P, int64_t n, int d, double *part, int nblk, double *stats,
@@ -113,6 +120,11 @@ cudaError_t launch_join_plain(const JoinLaunch &L, int grid, cudaStream_t s);
 int plain_ctas_per_sm(int d);
 size_t plain_smem_bytes(int d);
 cudaError_t launch_fp64_probe(double *out, int iters, int grid, cudaStream_t s);
+
+// ---- tensor-core filter (gj_tc.cu) -----------------------------------------
+int tc_prepare(gj_index *h, const double *stats_host, const int *perm, cudaStream_t s);
+cudaError_t launch_join_tc(const gj_index *h, const JoinLaunch &L, int grid, cudaStream_t s);
+size_t tc_staging_pairs_per_cta();
 
 }  // namespace gj
 
@@ -140,4 +152,11 @@ struct gj_index {
     int u;
     double e2, ew;
     int sms;
+    int qb;              // query block size the items were built with
+    // tensor-core filter operands (GJ_TC_FILTER)
+    bool tc_ready;
+    void *XA, *XB;       // fp16 [npad + 512][Kp] in core-matrix order
+    int tc_Kp;
+    int tc_Tbits;        // fp32 bits of the survivor threshold (scaled units)
+    double tc_sigma, tc_R0;
 };

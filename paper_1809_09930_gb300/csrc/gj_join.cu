@@ -377,11 +377,13 @@ cudaError_t launch_join_plain(const JoinLaunch &L, int grid, cudaStream_t s)
         e = cudaFuncSetAttribute(k_join_plain<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess)
             return e;
+        note_launch();
         k_join_plain<64><<<grid, JT, sm, s>>>(L);
     } else {
         e = cudaFuncSetAttribute(k_join_plain<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess)
             return e;
+        note_launch();
         k_join_plain<32><<<grid, JT, sm, s>>>(L);
     }
     return cudaGetLastError();

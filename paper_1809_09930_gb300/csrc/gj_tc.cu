@@ -1,0 +1,914 @@
+// gj_tc.cu -- tensor-core candidate filter with an exact FP64 recheck.
+//
+// No paper counterpart: the paper computes every candidate distance on the
+// FP32 cores (Sec. 4.4).  Here a candidate pair first meets a cheap,
+// conservative test on the 5th-generation tensor cores; only survivors get
+// the plain path's FP64 SHORTC distance, so the reported set is exactly the
+// plain path's set.
+//
+// Filter.  With a common centre c (per-dimension midrange) and a power-of-two
+// scale sigma, every point x gets fp16 coordinates h = rn16(sigma * (x - c)).
+// The A row of a query is [-2h, |h|^2_hi, |h|^2_lo, 1, 1, 0...] and the B row
+// of a candidate [h, 1, 1, |h|^2_hi, |h|^2_lo, 0...] (K = d + 4 padded to a
+// multiple of 16), so one fp16 x fp16 -> fp32 MMA gives
+//     t = |h_a|^2 + |h_b|^2 - 2 <h_a, h_b>  ~  sigma^2 |a - b|^2.
+// A pair is kept iff t <= T.  T bounds, for every pair within eps, the fp16
+// rounding of both points (|h - sigma(x-c)| <= 2^-11 |.| + 2^-25 per
+// coordinate), the hi/lo split of the norms (<= 2^-22 relative) and the fp32
+// accumulation (taken as <= (K+2) * 2^-22 * sum of |terms|, twice a
+// truncating adder's bound).  Every pair of R therefore survives.
+//
+// Kernel (one persistent CTA per SM, 320 threads):
+//   warp 0   producer: takes work items (query blocks of <= 248 points), loads
+//            the item's 256-row A tile and each 128-row candidate tile with
+//            bulk asynchronous copies (TMA) into a ring of shared-memory
+//            stages, and passes tile descriptors down a ring;
+//   warp 1   one thread issues tcgen05.mma (two M=128 x N=128 MMAs per K step,
+//            one per half of the query block) into a double-buffered TMEM
+//            accumulator (2 x 256 fp32 columns) and commits to mbarriers;
+//   warps 2-9 epilogue: read the accumulators with tcgen05.ld, reduce each
+//            32-column chunk with 3-input integer minima (t >= 0 compares as
+//            its bit pattern; negative rounding residue compares below T), and
+//            recheck survivors in FP64; exact pairs go to a double-buffered
+//            per-CTA staging area committed to the output per item (same
+//            resume protocol as the plain kernel).
+// Every wait is bounded (globaltimer); on timeout the CTA flags the error,
+// lets in-flight copies land, frees its TMEM and returns.
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "gj_internal.cuh"
+#include "gj_sm100.cuh"
+
+namespace gj {
+
+using namespace sm100;
+
+constexpr int TC_THREADS = 320;
+constexpr int TC_N = 128;        // candidate rows per tile
+constexpr int TC_M = 256;        // query rows per A tile (two M=128 halves)
+constexpr int TC_DR = 16;        // descriptor ring entries
+constexpr uint32_t TC_STG = 1u << 18;   // staging pairs per half per CTA (4 tiles of worst-case output)
+constexpr uint64_t TC_LIMIT_NS = 4000000000ull;   // 4 s per wait
+
+enum : uint32_t { F_FIRST = 1, F_LAST = 2, F_MARKER = 4, F_TRUNC = 8, F_TERM = 16, F_SELF = 32, F_FLUSH = 64 };
+
+struct TileDesc {
+    uint32_t item, tile, flags, pad;
+    uint32_t qbeg, qlen, qa, r0;
+    uint32_t ws, we, p2, p3;
+};
+
+struct TcShared {
+    uint64_t full_b[8], empty_b[8];
+    uint64_t full_a[2], empty_a[2];
+    uint64_t tmem_full[2], tmem_empty[2], desc_full[2];
+    uint64_t epi_bar[2];
+    TileDesc ring[TC_DR];
+    TileDesc tdesc[2];
+    uint32_t tmem_base;
+    uint32_t abort;
+    uint32_t flush_req;   // staging passed its soft limit: commit at the next flagged turn
+    uint32_t half;
+    uint32_t cnt[2];
+    uint32_t ok;
+    uint32_t pad;
+    unsigned long long base;
+};
+
+struct TcLaunch {
+    JoinLaunch J;
+    const unsigned char *XA;
+    const unsigned char *XB;
+    int Kp;
+    int NS;
+    int Tbits;
+    uint32_t a_bytes, b_bytes;
+    uint32_t off_b, off_s;
+};
+
+__device__ __forceinline__ int64_t tc_lower_u(const double *__restrict__ U, int64_t lo, int64_t hi, double ref,
+                                              double ew)
+{
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if (U[mid] - ref < -ew)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int64_t tc_upper_u(const double *__restrict__ U, int64_t lo, int64_t hi, double ref,
+                                              double ew)
+{
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if (U[mid] - ref <= ew)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+// Exact test of one surviving candidate: the plain path's FP64 SHORTC sum in
+// REORDER order.  Returns pairs emitted (0, 1 or 2).
+__device__ __noinline__ uint32_t tc_recheck(const TcLaunch *__restrict__ T, uint32_t qpos, uint32_t cpos,
+                                            gj_pair *stg, uint32_t *cnt, uint32_t *flush_req,
+                                            unsigned long long *counted)
+{
+    const double *__restrict__ X = T->J.ix.X;
+    const int64_t npad = T->J.ix.npad;
+    const int d = T->J.ix.d;
+    const long long e2bits = __double_as_longlong(T->J.ix.e2);
+    double s = 0.0;
+    for (int j = 0; j < d; ++j) {
+        double t = X[(int64_t)j * npad + qpos] - X[(int64_t)j * npad + cpos];
+        s = __fma_rn(t, t, s);
+        if (__double_as_longlong(s) > e2bits)
+            return 0;
+    }
+    const uint32_t n = (qpos != cpos) ? 2u : 1u;
+    if (stg == nullptr) {
+        *counted += n;
+        return n;
+    }
+    uint32_t off = atomicAdd(cnt, n);
+    if (off + n > TC_STG - 3u * 2u * 128u * 256u)
+        *(volatile uint32_t *)flush_req = 1u;
+    if (off + n > TC_STG) {
+        atomicOr(&T->J.ctl->err, kErrStaging);
+        return 0;
+    }
+    const uint32_t a = T->J.ix.orig[qpos], b = T->J.ix.orig[cpos];
+    stg[off] = gj_pair{a, b};
+    if (n == 2)
+        stg[off + 1] = gj_pair{b, a};
+    return n;
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    TcShared &S = *reinterpret_cast<TcShared *>(smem + T.off_s);
+    unsigned char *Abuf = smem;
+    unsigned char *Bbuf = smem + T.off_b;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const JoinLaunch &L = T.J;
+    const int NS = T.NS;
+    const bool count_only = (L.out == nullptr);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NS; ++s) {
+            mbar_init(&S.full_b[s], 1);
+            mbar_init(&S.empty_b[s], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&S.full_a[i], 1);
+            mbar_init(&S.empty_a[i], 1);
+            mbar_init(&S.tmem_full[i], 1);
+            mbar_init(&S.tmem_empty[i], 8);
+            mbar_init(&S.desc_full[i], 1);
+            mbar_init(&S.epi_bar[i], 8);
+        }
+        S.abort = 0;
+        S.flush_req = 0;
+        S.half = 0;
+        S.cnt[0] = S.cnt[1] = 0;
+        fence_mbar_init();
+    }
+    if (warp == 1) {
+        tmem_alloc(&S.tmem_base, 512);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = S.tmem_base;
+    volatile uint32_t *abort = &S.abort;
+
+    if (warp == 0) {
+        // ------------------------------------------------------------ producer
+        uint32_t seq = 0, nitem = 0;
+        bool dead = false;
+        auto push = [&](const TileDesc &D, bool tile) -> bool {   // lane 0 only
+            const uint32_t stage = seq % (uint32_t)NS;
+            if (!mbar_wait(&S.empty_b[stage], ((seq / NS) & 1u) ^ 1u, abort, TC_LIMIT_NS))
+                return false;
+            S.ring[seq % TC_DR] = D;
+            if (tile) {
+                mbar_arrive_expect_tx(&S.full_b[stage], T.b_bytes);
+                bulk_g2s(Bbuf + (size_t)stage * T.b_bytes, T.XB + (size_t)D.r0 * T.Kp * 2, T.b_bytes,
+                         &S.full_b[stage]);
+            } else {
+                mbar_arrive(&S.full_b[stage]);
+            }
+            ++seq;
+            return true;
+        };
+        for (;;) {
+            uint32_t item = 0xffffffffu, resume = 0;
+            if (lane == 0) {
+                if (count_only || !*(volatile unsigned int *)&L.ctl->full) {
+                    uint32_t t = (L.n_din > 0) ? atomicAdd(&L.ctl->din_head, 1u) : 0xffffffffu;
+                    if (t < L.n_din) {
+                        item = L.din[t].item;
+                        resume = L.din[t].tile;
+                    } else {
+                        uint32_t hq = atomicAdd(&L.ctl->head, 1u);
+                        if (hq < L.qlimit)
+                            item = L.queue[hq];
+                    }
+                }
+            }
+            item = __shfl_sync(0xffffffffu, item, 0);
+            resume = __shfl_sync(0xffffffffu, resume, 0);
+            if (item == 0xffffffffu || *abort)
+                break;
+            const Item it = L.ix.items[item];
+            const uint32_t qa = it.qbeg & ~7u;
+            const uint32_t abuf = nitem & 1u;
+            if (lane == 0) {
+                if (!mbar_wait(&S.empty_a[abuf], ((nitem >> 1) & 1u) ^ 1u, abort, TC_LIMIT_NS)) {
+                    dead = true;
+                } else {
+                    mbar_arrive_expect_tx(&S.full_a[abuf], T.a_bytes);
+                    bulk_g2s(Abuf + (size_t)abuf * T.a_bytes, T.XA + (size_t)qa * T.Kp * 2, T.a_bytes,
+                             &S.full_a[abuf]);
+                }
+            }
+            dead = __shfl_sync(0xffffffffu, dead, 0);
+            if (dead)
+                break;
+            ++nitem;
+            const int64_t cell_end = L.ix.cell_start[it.cell + 1];
+            const int64_t nb_begin = L.ix.adj_start[it.cell], nb_end = L.ix.adj_start[it.cell + 1];
+            const int u = L.ix.u;
+            double ulo = 0.0, uhi = 0.0;
+            if (u >= 0) {
+                ulo = L.ix.X[(int64_t)u * L.ix.npad + it.qbeg];
+                uhi = L.ix.X[(int64_t)u * L.ix.npad + it.qbeg + it.qlen - 1];
+            }
+            uint32_t tile_idx = 0;
+            bool have = false, first = true, trunc = false;
+            TileDesc pend{};
+            for (int64_t nb0 = nb_begin; nb0 < nb_end && !trunc && !dead; nb0 += 32) {
+                int64_t ws = 0, we = 0;
+                uint32_t b = 0;
+                if (nb0 + lane < nb_end) {
+                    b = L.ix.adj[nb0 + lane];
+                    if (b == it.cell) {
+                        ws = it.qbeg;
+                        we = cell_end;
+                    } else {
+                        ws = L.ix.cell_start[b];
+                        we = L.ix.cell_start[b + 1];
+                    }
+                    if (u >= 0) {
+                        const double *U = L.ix.X + (int64_t)u * L.ix.npad;
+                        ws = tc_lower_u(U, ws, we, ulo, L.ix.ew);
+                        we = tc_upper_u(U, ws, we, uhi, L.ix.ew);
+                    }
+                }
+                const int nw = (int)min((int64_t)32, nb_end - nb0);
+                for (int w = 0; w < nw && !trunc && !dead; ++w) {
+                    const int64_t s0 = __shfl_sync(0xffffffffu, ws, w);
+                    const int64_t e0 = __shfl_sync(0xffffffffu, we, w);
+                    const uint32_t bw = __shfl_sync(0xffffffffu, b, w);
+                    if (s0 >= e0)
+                        continue;
+                    for (int64_t r0 = s0 & ~(int64_t)7; r0 < e0; r0 += TC_N, ++tile_idx) {
+                        if (tile_idx < resume)
+                            continue;
+                        if (lane == 0) {
+                            if (!count_only && *(volatile unsigned int *)&L.ctl->full) {
+                                trunc = true;
+                            } else {
+                                if (have) {
+                                    if (first)
+                                        pend.flags |= F_FIRST;
+                                    first = false;
+                                    if (!push(pend, true))
+                                        dead = true;
+                                }
+                                pend = TileDesc{item, tile_idx, (bw == it.cell) ? F_SELF : 0u, 0u,
+                                                it.qbeg, it.qlen, qa, (uint32_t)r0,
+                                                (uint32_t)s0, (uint32_t)e0, 0u, 0u};
+                                have = true;
+                            }
+                        }
+                        trunc = __shfl_sync(0xffffffffu, trunc, 0);
+                        dead = __shfl_sync(0xffffffffu, dead, 0);
+                        if (trunc || dead)
+                            break;
+                    }
+                }
+            }
+            if (lane == 0 && !dead) {
+                if (have && !trunc) {
+                    pend.flags |= F_LAST | (first ? F_FIRST : 0u);
+                    if (!push(pend, true))
+                        dead = true;
+                } else {
+                    TileDesc M{item, first ? resume : 0u, F_MARKER | F_LAST | (first ? F_FIRST : 0u) |
+                                                         (trunc ? F_TRUNC : 0u),
+                               0u, it.qbeg, it.qlen, qa, 0u, 0u, 0u, 0u, 0u};
+                    if (!push(M, false))
+                        dead = true;
+                }
+            }
+            dead = __shfl_sync(0xffffffffu, dead, 0);
+            trunc = __shfl_sync(0xffffffffu, trunc, 0);
+            if (trunc || dead)
+                break;
+        }
+        if (lane == 0) {
+            if (!dead) {
+                TileDesc Tm{};
+                Tm.flags = F_TERM;
+                if (!push(Tm, false))
+                    dead = true;
+            }
+            if (dead) {
+                S.abort = 1;
+                atomicOr(&L.ctl->err, kErrTimeout);
+            }
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        // ------------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            const uint32_t idesc = idesc_f16_f32(128, TC_N);
+            const uint32_t lbo = 128, sbo = (uint32_t)T.Kp * 16;
+            const uint32_t a0 = smem_addr(Abuf), b0 = smem_addr(Bbuf);
+            const int ksteps = T.Kp / 16;
+            uint32_t seq = 0, turn = 0, nitem = 0, abuf = 0;
+            bool dead = false;
+            for (;;) {
+                const uint32_t stage = seq % (uint32_t)NS;
+                if (!mbar_wait(&S.full_b[stage], (seq / NS) & 1u, abort, TC_LIMIT_NS)) {
+                    dead = true;
+                    break;
+                }
+                const TileDesc D = S.ring[seq % TC_DR];
+                const uint32_t acc = turn & 1u;
+                if (!mbar_wait(&S.tmem_empty[acc], ((turn >> 1) & 1u) ^ 1u, abort, TC_LIMIT_NS)) {
+                    dead = true;
+                    break;
+                }
+                TileDesc Dm = D;
+                if (*(volatile uint32_t *)&S.flush_req)
+                    Dm.flags |= F_FLUSH;
+                S.tdesc[acc] = Dm;
+                if (D.flags & F_FIRST) {
+                    abuf = nitem & 1u;
+                    if (!mbar_wait(&S.full_a[abuf], (nitem >> 1) & 1u, abort, TC_LIMIT_NS)) {
+                        dead = true;
+                        break;
+                    }
+                    ++nitem;
+                }
+                if (!(D.flags & (F_MARKER | F_TERM))) {
+                    tc_fence_after();
+                    const uint32_t abase = a0 + abuf * T.a_bytes, bbase = b0 + stage * T.b_bytes;
+                    for (int h = 0; h < 2; ++h) {
+                        const uint32_t dcol = tmem + acc * 256u + (uint32_t)h * 128u;
+                        const uint32_t ah = abase + (uint32_t)h * (T.a_bytes / 2);
+                        for (int ks = 0; ks < ksteps; ++ks)
+                            mma_f16(dcol, desc_kmajor(ah + ks * 256u, lbo, sbo),
+                                    desc_kmajor(bbase + ks * 256u, lbo, sbo), idesc, ks > 0 ? 1u : 0u);
+                    }
+                    mma_commit(&S.empty_b[stage]);
+                    if (D.flags & F_LAST)
+                        mma_commit(&S.empty_a[abuf]);
+                    mbar_arrive(&S.desc_full[acc]);
+                    mma_commit(&S.tmem_full[acc]);
+                } else {
+                    mbar_arrive(&S.empty_b[stage]);
+                    if (D.flags & F_LAST)
+                        mma_commit(&S.empty_a[abuf]);
+                    mbar_arrive(&S.desc_full[acc]);
+                    mbar_arrive(&S.tmem_full[acc]);
+                }
+                ++seq;
+                ++turn;
+                if (D.flags & F_TERM)
+                    break;
+            }
+            if (dead) {
+                S.abort = 1;
+                atomicOr(&L.ctl->err, kErrTimeout);
+            }
+        }
+        __syncwarp();
+    } else {
+        // ------------------------------------------------------------ epilogue
+        const int e = warp - 2, q = warp & 3, hh = e >> 2;
+        const int etid = threadIdx.x - 64;
+        const unsigned lt = (1u << lane) - 1u;
+        (void)lt;
+        uint32_t turn = 0, es = 0, commit_tile = 0;
+        bool failed = false, dead = false;
+        unsigned long long surv = 0, counted = 0, slots = 0;
+        const int Tb = T.Tbits;
+        gj_pair *stg0 = count_only ? nullptr : L.staging + (size_t)blockIdx.x * 2 * TC_STG;
+        // Cross-warp agreement only where a decision is needed: at the end of
+        // an item and when the MMA thread flags a flush in the descriptor (a
+        // uniform signal).  Two barriers: A (every warp finished the tile),
+        // read the shared counters, leader reserves and flips the staging
+        // half, B (every warp has read); then the old half is copied out
+        // while later tiles write the new half.
+        auto epi_sync = [&]() -> bool {
+            __threadfence_block();
+            __syncwarp();
+            uint64_t *b = &S.epi_bar[es & 1u];
+            if (lane == 0)
+                mbar_arrive(b);
+            bool ok = mbar_wait(b, (es >> 1) & 1u, abort, TC_LIMIT_NS);
+            ++es;
+            return ok;
+        };
+        for (;;) {
+            const uint32_t acc = turn & 1u, par = (turn >> 1) & 1u;
+            if (!mbar_wait(&S.desc_full[acc], par, abort, TC_LIMIT_NS) ||
+                !mbar_wait(&S.tmem_full[acc], par, abort, TC_LIMIT_NS)) {
+                dead = true;
+                break;
+            }
+            tc_fence_after();
+            const TileDesc D = S.tdesc[acc];
+            if (D.flags & F_FIRST) {
+                commit_tile = D.tile;
+                failed = false;
+            }
+            const bool is_tile = !(D.flags & (F_MARKER | F_TERM));
+            const uint32_t half = S.half;
+            gj_pair *stg = stg0 ? stg0 + (size_t)half * TC_STG : nullptr;
+            if (is_tile && !failed) {
+                const uint32_t row = (uint32_t)(hh * 128 + q * 32 + lane);
+                const uint32_t qpos = D.qa + row;
+                const bool rvalid = qpos >= D.qbeg && qpos < D.qbeg + D.qlen;
+                const uint32_t tb = tmem + ((uint32_t)(q * 32) << 16) + acc * 256u + (uint32_t)hh * 128u;
+#pragma unroll 1
+                for (int c = 0; c < 4; ++c) {
+                    uint32_t v[32];
+                    tmem_ld32(tb + (uint32_t)c * 32u, v);
+                    tmem_wait_ld();
+                    int m = __vimin3_s32((int)v[0], (int)v[1], (int)v[2]);
+#pragma unroll
+                    for (int i = 3; i < 31; i += 2)
+                        m = __vimin3_s32(m, (int)v[i], (int)v[i + 1]);
+                    m = min(m, (int)v[31]);
+                    const bool hit = rvalid && m <= Tb;
+                    if (__any_sync(0xffffffffu, hit)) {
+                        if (hit) {
+#pragma unroll
+                            for (int i = 0; i < 32; ++i) {
+                                if ((int)v[i] <= Tb) {
+                                    const uint32_t cpos = D.r0 + (uint32_t)(c * 32 + i);
+                                    if (cpos >= D.ws && cpos < D.we && (!(D.flags & F_SELF) || cpos >= qpos)) {
+                                        ++surv;
+                                        tc_recheck(&T, qpos, cpos, stg, &S.cnt[half], &S.flush_req, &counted);
+                                    }
+                                }
+                            }
+                        }
+                    }
+                }
+                if (etid == 0) {
+                    const uint32_t lo = max(D.r0, D.ws), hi = min(D.r0 + (uint32_t)TC_N, D.we);
+                    slots += (unsigned long long)D.qlen * (hi > lo ? hi - lo : 0u);
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0)
+                mbar_arrive(&S.tmem_empty[acc]);
+            ++turn;
+            if (D.flags & F_TERM)
+                break;
+            if (count_only)
+                continue;
+            const bool item_end = (D.flags & (F_LAST | F_MARKER)) != 0;
+            const bool flush = (D.flags & F_FLUSH) != 0;
+            if (!item_end && !flush)
+                continue;
+            if (!epi_sync()) {   // A
+                dead = true;
+                break;
+            }
+            const uint32_t cnt = S.cnt[half];
+            const bool commit = !failed && !(D.flags & F_TRUNC);
+            if (etid == 0) {
+                uint32_t ok = 0;
+                unsigned long long b = 0;
+                if (commit) {
+                    ok = 1;
+                    if (cnt) {
+                        b = atomicAdd(&L.ctl->pos, (unsigned long long)cnt);
+                        ok = (b + cnt <= L.cap) ? 1u : 0u;
+                        if (!ok) {
+                            atomicMin(&L.ctl->fail_base, b);
+                            atomicExch(&L.ctl->full, 1u);
+                        }
+                    }
+                }
+                if (item_end && !(commit && ok)) {
+                    uint32_t slot = atomicAdd(&L.ctl->dout_n, 1u);
+                    if (slot < L.dout_cap)
+                        L.dout[slot] = Deferred{D.item, commit_tile};
+                    else
+                        atomicOr(&L.ctl->err, kErrDeferred);
+                }
+                S.ok = ok;
+                S.base = b;
+                S.cnt[half ^ 1u] = 0;
+                S.half = half ^ 1u;
+                S.flush_req = 0;
+            }
+            if (!epi_sync()) {   // B
+                dead = true;
+                break;
+            }
+            if (commit) {
+                if (S.ok) {
+                    const unsigned long long b = S.base;
+                    for (uint32_t i = (uint32_t)etid; i < cnt; i += 256u)
+                        L.out[b + i] = stg[i];
+                    if (!item_end && is_tile)
+                        commit_tile = D.tile + 1;
+                } else {
+                    failed = true;
+                }
+            }
+        }
+        if (dead) {
+            S.abort = 1;
+            atomicOr(&L.ctl->err, kErrTimeout);
+        }
+        for (int o = 16; o; o >>= 1) {
+            surv += __shfl_xor_sync(0xffffffffu, surv, o);
+            counted += __shfl_xor_sync(0xffffffffu, counted, o);
+        }
+        if (lane == 0) {
+            if (surv)
+                atomicAdd(&L.ctl->survivors, surv);
+            if (counted)
+                atomicAdd(&L.ctl->counted, counted);
+        }
+        if (etid == 0 && slots)
+            atomicAdd(&L.ctl->evaluated, slots);
+    }
+
+    __syncthreads();
+    if (S.abort) {
+        // let copies and MMAs already issued land before the memory goes away
+        const uint64_t t0 = globaltimer();
+        while (globaltimer() - t0 < 2000000ull) {
+        }
+    }
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem, 512);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Operand preparation
+// ---------------------------------------------------------------------------
+struct TcPrepParams {
+    int d, Kp;
+    double sigma;
+    const double *centre;   // device, reordered dims
+};
+
+__global__ void k_tc_radius(const double *__restrict__ X, int64_t n, int64_t npad, int d,
+                            const double *__restrict__ centre, unsigned long long *__restrict__ rmax)
+{
+    int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    double r2 = 0.0;
+    if (p < n)
+        for (int j = 0; j < d; ++j) {
+            double t = X[(int64_t)j * npad + p] - centre[j];
+            r2 = __fma_rn(t, t, r2);
+        }
+    for (int o = 16; o; o >>= 1)
+        r2 = fmax(r2, __shfl_xor_sync(0xffffffffu, r2, o));
+    if ((threadIdx.x & 31) == 0)
+        atomicMax(rmax, (unsigned long long)__double_as_longlong(r2));
+}
+
+__device__ __forceinline__ __half tc_coord(const double *__restrict__ X, int64_t npad, int64_t p, int j,
+                                           const double *__restrict__ centre, double sigma)
+{
+    return __double2half((X[(int64_t)j * npad + p] - centre[j]) * sigma);
+}
+
+// XA/XB: row p at core matrix ((p/8)*(Kp/8) + k/8), row p%8, element k%8.
+__global__ void k_tc_pack(const double *__restrict__ X, int64_t n, int64_t npad, TcPrepParams P,
+                          uint4 *__restrict__ XA, uint4 *__restrict__ XB)
+{
+    int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= n)
+        return;
+    const int d = P.d, Kp = P.Kp;
+    double nrm = 0.0;
+    for (int j = 0; j < d; ++j) {
+        double h = (double)__half2float(tc_coord(X, npad, p, j, P.centre, P.sigma));
+        nrm = __fma_rn(h, h, nrm);
+    }
+    const __half hi = __double2half(nrm);
+    const __half lo = __double2half(nrm - (double)__half2float(hi));
+    const __half one = __float2half(1.0f), zero = __float2half(0.0f);
+    for (int kc = 0; kc < Kp / 8; ++kc) {
+        __align__(16) __half a[8], b[8];
+        for (int e = 0; e < 8; ++e) {
+            const int k = kc * 8 + e;
+            if (k < d) {
+                __half h = tc_coord(X, npad, p, k, P.centre, P.sigma);
+                b[e] = h;
+                a[e] = __float2half(-2.0f * __half2float(h));
+            } else if (k == d) {
+                a[e] = hi;
+                b[e] = one;
+            } else if (k == d + 1) {
+                a[e] = lo;
+                b[e] = one;
+            } else if (k == d + 2) {
+                a[e] = one;
+                b[e] = hi;
+            } else if (k == d + 3) {
+                a[e] = one;
+                b[e] = lo;
+            } else {
+                a[e] = zero;
+                b[e] = zero;
+            }
+        }
+        const int64_t idx = ((p >> 3) * (Kp / 8) + kc) * 8 + (p & 7);   // in 16-byte units
+        XA[idx] = *reinterpret_cast<const uint4 *>(a);
+        XB[idx] = *reinterpret_cast<const uint4 *>(b);
+    }
+}
+
+// Survivor threshold in scaled units (see the file header for the terms).
+static double tc_threshold(double eps, double sigma, double R0, int d, int Kp)
+{
+    const double sd = sqrt((double)d);
+    const double Rh = sigma * R0 * (1.0 + ldexp(1.0, -10)) + sd * ldexp(1.0, -24);
+    const double quant = 2.0 * (ldexp(1.0, -11) * Rh + sd * ldexp(1.0, -25));
+    const double D = sigma * eps * (1.0 + ldexp(1.0, -40)) + quant * (1.0 + ldexp(1.0, -40));
+    const double E = (Kp + 2) * ldexp(1.0, -22) * 4.04 * Rh * Rh + 2.0 * ldexp(1.0, -21) * Rh * Rh * 1.01 +
+                     (2.0 * d + 8.0) * ldexp(1.0, -50) * Rh * Rh;
+    return (D * D + E) * (1.0 + ldexp(1.0, -20));
+}
+
+int tc_prepare(gj_index *h, const double *stats_host, const int *perm, cudaStream_t s)
+{
+    const int d = h->info.d;
+    const int64_t n = h->info.n;
+    const int Kp = ((d + 4 + 15) / 16) * 16;
+    if (Kp > 128 || n == 0) {
+        h->tc_ready = false;
+        return GJ_OK;
+    }
+    std::vector<double> c(d);
+    for (int j = 0; j < d; ++j)
+        c[j] = 0.5 * (stats_host[(size_t)perm[j] * 4 + 2] + stats_host[(size_t)perm[j] * 4 + 3]);
+    double *centre = nullptr;
+    unsigned long long *rmax = nullptr;
+    cudaError_t e = cudaMalloc(&centre, d * sizeof(double));
+    if (e == cudaSuccess)
+        e = cudaMalloc(&rmax, sizeof(unsigned long long));
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(centre, c.data(), d * sizeof(double), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(rmax, 0, sizeof(unsigned long long), s);
+    unsigned long long rbits = 0;
+    if (e == cudaSuccess) {
+        note_launch();
+        k_tc_radius<<<(int)((n + 255) / 256), 256, 0, s>>>(h->X, n, h->npad, d, centre, rmax);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&rbits, rmax, sizeof(rbits), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(s);
+    double R2 = 0.0;
+    memcpy(&R2, &rbits, sizeof(R2));
+    const double R0 = sqrt(R2) * (1.0 + ldexp(1.0, -30));
+    int sexp = 0;
+    if (R0 > 0.0)
+        sexp = (int)floor(log2(250.0 / R0));
+    const double sigma = ldexp(1.0, sexp);
+    const int64_t rows = h->npad + 512;
+    const size_t bytes = (size_t)rows * Kp * 2;
+    if (e == cudaSuccess)
+        e = cudaMalloc(&h->XA, bytes);
+    if (e == cudaSuccess)
+        e = cudaMalloc(&h->XB, bytes);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(h->XA, 0, bytes, s);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(h->XB, 0, bytes, s);
+    if (e == cudaSuccess) {
+        TcPrepParams P{d, Kp, sigma, centre};
+        note_launch();
+        k_tc_pack<<<(int)((n + 127) / 128), 128, 0, s>>>(h->X, n, h->npad, P, (uint4 *)h->XA, (uint4 *)h->XB);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(s);
+    cudaFree(centre);
+    cudaFree(rmax);
+    if (e != cudaSuccess)
+        return e == cudaErrorMemoryAllocation ? GJ_ERR_OOM : GJ_ERR_CUDA;
+    const double Td = tc_threshold(h->info.eps, sigma, R0, d, Kp);
+    float Tf = (float)Td;
+    if ((double)Tf < Td)
+        Tf = nextafterf(Tf, INFINITY);
+    int Tb;
+    memcpy(&Tb, &Tf, sizeof(Tb));
+    h->tc_Kp = Kp;
+    h->tc_Tbits = Tb;
+    h->tc_sigma = sigma;
+    h->tc_R0 = R0;
+    h->tc_ready = true;
+    return GJ_OK;
+}
+
+static int tc_stages(int Kp, uint32_t *a_bytes, uint32_t *b_bytes, uint32_t *off_b, uint32_t *off_s,
+                     size_t *smem)
+{
+    *a_bytes = (uint32_t)TC_M * Kp * 2;
+    *b_bytes = (uint32_t)TC_N * Kp * 2;
+    const size_t budget = 227 * 1024 - 1024;
+    const size_t fixed = 2 * (size_t)(*a_bytes) + ((sizeof(TcShared) + 1023) & ~size_t(1023));
+    int ns = (int)((budget - fixed) / *b_bytes);
+    if (ns > 8)
+        ns = 8;
+    *off_b = 2 * *a_bytes;
+    *off_s = *off_b + (uint32_t)ns * *b_bytes;
+    *smem = *off_s + sizeof(TcShared);
+    if (*smem < 120 * 1024)
+        *smem = 120 * 1024;   // one CTA per SM: each holds all 512 TMEM columns
+    return ns;
+}
+
+size_t tc_staging_pairs_per_cta() { return 2 * (size_t)TC_STG; }
+
+cudaError_t launch_join_tc(const gj_index *h, const JoinLaunch &L, int grid, cudaStream_t s)
+{
+    TcLaunch T{};
+    T.J = L;
+    T.XA = (const unsigned char *)h->XA;
+    T.XB = (const unsigned char *)h->XB;
+    T.Kp = h->tc_Kp;
+    T.Tbits = h->tc_Tbits;
+    size_t sm = 0;
+    T.NS = tc_stages(T.Kp, &T.a_bytes, &T.b_bytes, &T.off_b, &T.off_s, &sm);
+    if (T.NS < 2)
+        return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(k_join_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess)
+        return e;
+    note_launch();
+    k_join_tc<<<grid, TC_THREADS, sm, s>>>(T);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Diagnostic: one 128x128 tile D = A * B^T through the same operand layout,
+// descriptors and TMEM path as the join (used by the tests to check the
+// layout and the accumulation error model).
+// ---------------------------------------------------------------------------
+__global__ void k_tc_debug(const unsigned char *__restrict__ A, const unsigned char *__restrict__ B, int Kp,
+                           float *__restrict__ D, unsigned int *__restrict__ err)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ uint64_t bar_ld, bar_mma;
+    __shared__ uint32_t tbase, abort_flag;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t bytes = 128u * Kp * 2;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar_ld, 1);
+        mbar_init(&bar_mma, 1);
+        abort_flag = 0;
+        fence_mbar_init();
+    }
+    if (warp == 0) {
+        tmem_alloc(&tbase, 128);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tbase;
+    bool ok = true;
+    if (threadIdx.x == 0) {
+        mbar_arrive_expect_tx(&bar_ld, 2 * bytes);
+        bulk_g2s(smem, A, bytes, &bar_ld);
+        bulk_g2s(smem + bytes, B, bytes, &bar_ld);
+        ok = mbar_wait(&bar_ld, 0, &abort_flag, TC_LIMIT_NS);
+        if (ok) {
+            tc_fence_after();
+            const uint32_t a0 = smem_addr(smem), b0 = a0 + bytes;
+            const uint32_t idesc = idesc_f16_f32(128, 128);
+            for (int ks = 0; ks < Kp / 16; ++ks)
+                mma_f16(tmem, desc_kmajor(a0 + ks * 256u, 128, Kp * 16), desc_kmajor(b0 + ks * 256u, 128, Kp * 16),
+                        idesc, ks > 0 ? 1u : 0u);
+            mma_commit(&bar_mma);
+        } else {
+            abort_flag = 1;
+        }
+    }
+    __syncthreads();
+    if (!abort_flag) {
+        if (mbar_wait(&bar_mma, 0, &abort_flag, TC_LIMIT_NS)) {
+            tc_fence_after();
+            const int row = warp * 32 + lane;
+            for (int c = 0; c < 4; ++c) {
+                uint32_t v[32];
+                tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + c * 32u, v);
+                tmem_wait_ld();
+                for (int i = 0; i < 32; ++i)
+                    D[row * 128 + c * 32 + i] = __uint_as_float(v[i]);
+            }
+        } else {
+            atomicOr(err, 1u);
+        }
+    } else {
+        atomicOr(err, 1u);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (abort_flag) {
+        const uint64_t t0 = globaltimer();
+        while (globaltimer() - t0 < 2000000ull) {
+        }
+    }
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem, 128);
+    }
+}
+
+}  // namespace gj
+
+extern "C" int gj_debug_tc_tile(const uint16_t *A, const uint16_t *B, int32_t Kp, float *D)
+{
+    using namespace gj;
+    if (!A || !B || !D || Kp < 16 || Kp > 128 || Kp % 16)
+        return GJ_ERR_INVALID_ARG;
+    int dev = 0;
+    cudaDeviceProp prop;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess ||
+        prop.major != 10 || prop.minor != 3)
+        return GJ_ERR_UNSUPPORTED;
+    // pack row-major [128][Kp] into the core-matrix layout
+    std::vector<uint16_t> pa((size_t)128 * Kp), pb((size_t)128 * Kp);
+    for (int r = 0; r < 128; ++r)
+        for (int k = 0; k < Kp; ++k) {
+            size_t idx = (((size_t)(r >> 3) * (Kp / 8) + (k >> 3)) * 8 + (r & 7)) * 8 + (k & 7);
+            pa[idx] = A[(size_t)r * Kp + k];
+            pb[idx] = B[(size_t)r * Kp + k];
+        }
+    unsigned char *dA = nullptr, *dB = nullptr;
+    float *dD = nullptr;
+    unsigned int *derr = nullptr, herr = 0;
+    const size_t bytes = (size_t)128 * Kp * 2;
+    cudaError_t e = cudaMalloc(&dA, bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&dB, bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&dD, 128 * 128 * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&derr, sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMemcpy(dA, pa.data(), bytes, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dB, pb.data(), bytes, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(derr, 0, sizeof(unsigned int));
+    if (e == cudaSuccess) {
+        const int sm = (int)(2 * bytes);
+        e = cudaFuncSetAttribute(k_tc_debug, cudaFuncAttributeMaxDynamicSharedMemorySize, sm < 48 * 1024 ? 48 * 1024 : sm);
+        if (e == cudaSuccess) {
+            note_launch();
+            k_tc_debug<<<1, 128, sm < 48 * 1024 ? 48 * 1024 : sm>>>(dA, dB, Kp, dD, derr);
+            e = cudaGetLastError();
+        }
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(D, dD, 128 * 128 * sizeof(float), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(&herr, derr, sizeof(herr), cudaMemcpyDeviceToHost);
+    cudaFree(dA);
+    cudaFree(dB);
+    cudaFree(dD);
+    cudaFree(derr);
+    if (e != cudaSuccess)
+        return GJ_ERR_CUDA;
+    return herr ? GJ_ERR_TIMEOUT : GJ_OK;
+}

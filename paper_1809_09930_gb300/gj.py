@@ -63,7 +63,8 @@ class gj_join_stats(C.Structure):
 
 EXPORTS = ["gj_config_init", "gj_index_build", "gj_index_build_ex", "gj_self_join",
            "gj_self_join_part", "gj_index_get_info", "gj_last_join_stats", "gj_free",
-           "gj_last_status", "gj_status_string", "gj_version", "gj_probe_fp64_tflops"]
+           "gj_last_status", "gj_status_string", "gj_version", "gj_probe_fp64_tflops",
+           "gj_kernel_launches", "gj_debug_tc_tile"]
 
 _lib = None
 
@@ -102,6 +103,10 @@ def load(path: str | None = None):
     lib.gj_version.argtypes = []
     lib.gj_probe_fp64_tflops.restype = C.c_int
     lib.gj_probe_fp64_tflops.argtypes = [C.c_int32, C.POINTER(C.c_double)]
+    lib.gj_kernel_launches.restype = C.c_ulonglong
+    lib.gj_kernel_launches.argtypes = []
+    lib.gj_debug_tc_tile.restype = C.c_int
+    lib.gj_debug_tc_tile.argtypes = [V, V, C.c_int32, V]
     if path is None:
         _lib = lib
     return lib
@@ -233,6 +238,23 @@ def gj_probe_fp64_tflops(device: int = -1) -> float:
     if st != GJ_OK:
         raise GJError(st, "gj_probe_fp64_tflops")
     return float(v.value)
+
+
+def gj_kernel_launches() -> int:
+    return int(load().gj_kernel_launches())
+
+
+def gj_debug_tc_tile(A, B) -> np.ndarray:
+    """D = A @ B.T on the tensor cores for (128, Kp) float16 arrays."""
+    A = np.ascontiguousarray(A, dtype=np.float16)
+    B = np.ascontiguousarray(B, dtype=np.float16)
+    if A.shape != B.shape or A.shape[0] != 128:
+        raise ValueError("A and B must both be (128, Kp) float16")
+    D = np.empty((128, 128), dtype=np.float32)
+    st = load().gj_debug_tc_tile(A.ctypes.data, B.ctypes.data, A.shape[1], D.ctypes.data)
+    if st != GJ_OK:
+        raise GJError(st, "gj_debug_tc_tile")
+    return D
 
 
 # ---------------------------------------------------------------------------
