@@ -56,6 +56,7 @@ constexpr int TC_M = 256;        // query rows per A tile (two M=128 halves)
 constexpr int TC_DR = 16;        // descriptor ring entries
 constexpr uint32_t TC_STG = 1u << 18;   // staging pairs per half per CTA (4 tiles of worst-case output)
 constexpr uint64_t TC_LIMIT_NS = 4000000000ull;   // 4 s per wait
+constexpr int TC_SQ = 64;        // survivor queue per epilogue warp
 
 enum : uint32_t { F_FIRST = 1, F_LAST = 2, F_MARKER = 4, F_TRUNC = 8, F_TERM = 16, F_SELF = 32, F_FLUSH = 64 };
 
@@ -80,6 +81,8 @@ struct TcShared {
     uint32_t ok;
     uint32_t pad;
     unsigned long long base;
+    uint32_t sq[8][TC_SQ];   // per epilogue warp: survivors waiting for the FP64 recheck
+    uint32_t sc[8][TC_SQ];
 };
 
 struct TcLaunch {
@@ -120,39 +123,84 @@ __device__ __forceinline__ int64_t tc_upper_u(const double *__restrict__ U, int6
 }
 
 // Exact test of one surviving candidate: the plain path's FP64 SHORTC sum in
-// REORDER order.  Returns pairs emitted (0, 1 or 2).
-__device__ __noinline__ uint32_t tc_recheck(const TcLaunch *__restrict__ T, uint32_t qpos, uint32_t cpos,
-                                            gj_pair *stg, uint32_t *cnt, uint32_t *flush_req,
-                                            unsigned long long *counted)
+// REORDER order (same operations in the same order, so the same decision).
+// Coordinates are fetched 16 dimensions at a time with independent loads, so
+// a recheck costs about d/16 memory round trips instead of d.
+__device__ __forceinline__ bool tc_exact(const double *__restrict__ X, int64_t npad, int d, long long e2bits,
+                                         uint32_t qpos, uint32_t cpos)
 {
+    double s = 0.0;
+    for (int j0 = 0; j0 < d; j0 += 16) {
+        double a[16], b[16];
+#pragma unroll
+        for (int t = 0; t < 16; ++t) {
+            if (j0 + t < d) {
+                a[t] = X[(int64_t)(j0 + t) * npad + qpos];
+                b[t] = X[(int64_t)(j0 + t) * npad + cpos];
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < 16; ++t) {
+            if (j0 + t < d) {
+                const double dd = a[t] - b[t];
+                s = __fma_rn(dd, dd, s);
+                if (__double_as_longlong(s) > e2bits)
+                    return false;
+            }
+        }
+    }
+    return true;
+}
+
+// Recheck the warp's queued survivors (one per lane per round) and emit the
+// exact pairs into the staging half (or count them).  Called by all 32 lanes.
+__device__ __noinline__ void tc_flush_survivors(const TcLaunch *__restrict__ T, const uint32_t *sq,
+                                                const uint32_t *sc, uint32_t n, gj_pair *stg, uint32_t *cnt,
+                                                uint32_t *flush_req, unsigned long long *counted)
+{
+    const int lane = threadIdx.x & 31;
     const double *__restrict__ X = T->J.ix.X;
     const int64_t npad = T->J.ix.npad;
     const int d = T->J.ix.d;
     const long long e2bits = __double_as_longlong(T->J.ix.e2);
-    double s = 0.0;
-    for (int j = 0; j < d; ++j) {
-        double t = X[(int64_t)j * npad + qpos] - X[(int64_t)j * npad + cpos];
-        s = __fma_rn(t, t, s);
-        if (__double_as_longlong(s) > e2bits)
-            return 0;
+    for (uint32_t base = 0; base < n; base += 32) {
+        const uint32_t i = base + lane;
+        bool keep = false;
+        uint32_t qpos = 0, cpos = 0;
+        if (i < n) {
+            qpos = sq[i];
+            cpos = sc[i];
+            keep = tc_exact(X, npad, d, e2bits, qpos, cpos);
+        }
+        const uint32_t np = keep ? ((qpos != cpos) ? 2u : 1u) : 0u;
+        if (stg == nullptr) {
+            *counted += np;
+            continue;
+        }
+        uint32_t incl = np;
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o)
+                incl += y;
+        }
+        const uint32_t tot = __shfl_sync(0xffffffffu, incl, 31);
+        uint32_t off = 0;
+        if (lane == 0 && tot)
+            off = atomicAdd(cnt, tot);
+        off = __shfl_sync(0xffffffffu, off, 0) + incl - np;
+        if (tot) {
+            if (off + np > TC_STG - 3u * 2u * 128u * 256u)
+                *(volatile uint32_t *)flush_req = 1u;
+            if (off + np > TC_STG) {
+                atomicOr(&T->J.ctl->err, kErrStaging);
+            } else if (np) {
+                const uint32_t a = T->J.ix.orig[qpos], b = T->J.ix.orig[cpos];
+                stg[off] = gj_pair{a, b};
+                if (np == 2)
+                    stg[off + 1] = gj_pair{b, a};
+            }
+        }
     }
-    const uint32_t n = (qpos != cpos) ? 2u : 1u;
-    if (stg == nullptr) {
-        *counted += n;
-        return n;
-    }
-    uint32_t off = atomicAdd(cnt, n);
-    if (off + n > TC_STG - 3u * 2u * 128u * 256u)
-        *(volatile uint32_t *)flush_req = 1u;
-    if (off + n > TC_STG) {
-        atomicOr(&T->J.ctl->err, kErrStaging);
-        return 0;
-    }
-    const uint32_t a = T->J.ix.orig[qpos], b = T->J.ix.orig[cpos];
-    stg[off] = gj_pair{a, b};
-    if (n == 2)
-        stg[off + 1] = gj_pair{b, a};
-    return n;
 }
 
 __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
@@ -414,8 +462,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
         const int e = warp - 2, q = warp & 3, hh = e >> 2;
         const int etid = threadIdx.x - 64;
         const unsigned lt = (1u << lane) - 1u;
-        (void)lt;
-        uint32_t turn = 0, es = 0, commit_tile = 0;
+        uint32_t turn = 0, es = 0, commit_tile = 0, nq = 0;
         bool failed = false, dead = false;
         unsigned long long surv = 0, counted = 0, slots = 0;
         const int Tb = T.Tbits;
@@ -452,6 +499,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
             const bool is_tile = !(D.flags & (F_MARKER | F_TERM));
             const uint32_t half = S.half;
             gj_pair *stg = stg0 ? stg0 + (size_t)half * TC_STG : nullptr;
+            uint32_t *const sq = S.sq[e], *const sc = S.sc[e];
             if (is_tile && !failed) {
                 const uint32_t row = (uint32_t)(hh * 128 + q * 32 + lane);
                 const uint32_t qpos = D.qa + row;
@@ -469,16 +517,28 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
                     m = min(m, (int)v[31]);
                     const bool hit = rvalid && m <= Tb;
                     if (__any_sync(0xffffffffu, hit)) {
-                        if (hit) {
+                        // queue the chunk's survivors, column by column (warp-aggregated)
 #pragma unroll
-                            for (int i = 0; i < 32; ++i) {
-                                if ((int)v[i] <= Tb) {
-                                    const uint32_t cpos = D.r0 + (uint32_t)(c * 32 + i);
-                                    if (cpos >= D.ws && cpos < D.we && (!(D.flags & F_SELF) || cpos >= qpos)) {
-                                        ++surv;
-                                        tc_recheck(&T, qpos, cpos, stg, &S.cnt[half], &S.flush_req, &counted);
-                                    }
+                        for (int i = 0; i < 32; ++i) {
+                            const uint32_t cpos = D.r0 + (uint32_t)(c * 32 + i);
+                            const bool h = hit && (int)v[i] <= Tb && cpos >= D.ws && cpos < D.we &&
+                                           (!(D.flags & F_SELF) || cpos >= qpos);
+                            const unsigned bal = __ballot_sync(0xffffffffu, h);
+                            if (bal) {
+                                const uint32_t k = (uint32_t)__popc(bal);
+                                if (nq + k > (uint32_t)TC_SQ) {
+                                    __syncwarp();
+                                    tc_flush_survivors(&T, sq, sc, nq, stg, &S.cnt[half], &S.flush_req, &counted);
+                                    __syncwarp();
+                                    nq = 0;
                                 }
+                                if (h) {
+                                    const uint32_t at = nq + (uint32_t)__popc(bal & lt);
+                                    sq[at] = qpos;
+                                    sc[at] = cpos;
+                                }
+                                nq += k;
+                                surv += h ? 1 : 0;
                             }
                         }
                     }
@@ -493,12 +553,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
             if (lane == 0)
                 mbar_arrive(&S.tmem_empty[acc]);
             ++turn;
+            // the accumulator is released; recheck queued survivors now when the
+            // queue is half full, or when the item's results must be complete
+            const bool item_end = (D.flags & (F_LAST | F_MARKER)) != 0;
+            const bool flush = (D.flags & F_FLUSH) != 0;
+            if (nq >= 32u || ((item_end || flush || (D.flags & F_TERM)) && nq)) {
+                __syncwarp();
+                tc_flush_survivors(&T, sq, sc, nq, stg, &S.cnt[half], &S.flush_req, &counted);
+                __syncwarp();
+                nq = 0;
+            }
             if (D.flags & F_TERM)
                 break;
             if (count_only)
                 continue;
-            const bool item_end = (D.flags & (F_LAST | F_MARKER)) != 0;
-            const bool flush = (D.flags & F_FLUSH) != 0;
             if (!item_end && !flush)
                 continue;
             if (!epi_sync()) {   // A
