@@ -155,6 +155,38 @@ int gj_self_join(gj_index *h, gj_pair *pairs_out, uint64_t cap, uint64_t *count)
 int gj_self_join_part(gj_index *h, int32_t part, int32_t nparts, gj_pair *pairs_out,
                       uint64_t cap, uint64_t *count);
 
+/*
+ * A self-join that allocates nothing (no paper counterpart).  gj_self_join
+ * allocates its launch state (control block, work order, deferred lists,
+ * staging) with cudaMalloc on every call.  Callers whose device memory is
+ * reserved up front by a caching allocator, or whose latency budget forbids
+ * entering the driver's allocator during a join, cannot accept that; this entry
+ * point serves them.  It runs the plain FP64 join (not the tensor-core filter)
+ * and writes pairs straight into pairs_out, which must be device memory of the
+ * handle's device (NULL with cap == 0: count only).  Its scratch -- the
+ * control block and the dequeue order of the part's work items -- lives in one
+ * 4 MiB array in device global memory that the library declares at file scope;
+ * every GPU that loads the library holds that array until the process exits.
+ *   h, part, nparts  as gj_self_join_part (part = 0, nparts = 1: the whole R).
+ *   limit            at most (4 MiB - 256 B) / 4 = 1,048,512 work items in the
+ *                    part (about 125 million points in large cells); larger
+ *                    parts return GJ_ERR_TOO_LARGE.  Indices built with
+ *                    GJ_TC_FILTER return GJ_ERR_INVALID_ARG.
+ *   set-up           the first call on a device looks up the array's device
+ *                    address (cudaGetSymbolAddress) with that device current;
+ *                    make that first call before any stream capture.
+ *   sharing          all calls share the array and find the last call's
+ *                    contents (the call clears what must start at zero).
+ *                    Calls that overlap on the GPU race on it: do not run two
+ *                    at once, on any handle or stream of the same device.
+ * Returns as gj_self_join: GJ_OK, or GJ_ERR_CAPACITY with *count = |R| when
+ * |R| > cap (then pairs_out holds cap pairs of R), or another error code.
+ * The call itself allocates nothing: no cudaMalloc, no cudaFree, no event or
+ * stream creation.
+ */
+int gj_self_join_noalloc(const gj_index *h, int32_t part, int32_t nparts, gj_pair *pairs_out,
+                         uint64_t cap, uint64_t *count);
+
 /* Facts about the index (k used, REORDER permutation, cell and candidate counts). */
 int gj_index_get_info(const gj_index *h, gj_index_info_t *info);
 

@@ -117,6 +117,7 @@ int build_index(gj_index *h, const double *P, int64_t n, int d, double eps, int 
 
 // ---- join kernels (gj_join.cu) -------------------------------------------
 cudaError_t launch_join_plain(const JoinLaunch &L, int grid, cudaStream_t s);
+cudaError_t launch_join_plain_direct(const JoinLaunch &L, int grid, cudaStream_t s);
 int plain_ctas_per_sm(int d);
 size_t plain_smem_bytes(int d);
 cudaError_t launch_fp64_probe(double *out, int iters, int grid, cudaStream_t s);

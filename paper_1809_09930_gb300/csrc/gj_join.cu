@@ -74,7 +74,10 @@ __device__ __forceinline__ int64_t upper_u(const double *__restrict__ U, int64_t
     return lo;
 }
 
-template <int CT>
+// DIRECT = true: pairs go straight to the output through one global atomic
+// per warp (no staging, no commit/defer protocol); pairs past `cap` are
+// counted but not written.
+template <int CT, bool DIRECT = false>
 __global__ void __launch_bounds__(JT) k_join_plain(JoinLaunch L)
 {
     constexpr int LOGCT = (CT == 64) ? 6 : (CT == 32 ? 5 : 4);
@@ -90,7 +93,8 @@ __global__ void __launch_bounds__(JT) k_join_plain(JoinLaunch L)
     const double *__restrict__ X = L.ix.X;
     const long long e2bits = __double_as_longlong(L.ix.e2);
     const bool count_only = (L.out == nullptr);
-    gj_pair *stg = count_only ? nullptr : L.staging + (size_t)blockIdx.x * L.stg_cap;
+    const bool staged = !count_only && !DIRECT;
+    gj_pair *stg = staged ? L.staging + (size_t)blockIdx.x * L.stg_cap : nullptr;
     const uint32_t flush_at = L.stg_cap > 2u * QB * CT ? L.stg_cap - 2u * QB * CT : 0u;
 
     unsigned long long my_count = 0, my_dims = 0, my_pairs = 0;
@@ -253,6 +257,23 @@ __global__ void __launch_bounds__(JT) k_join_plain(JoinLaunch L)
                                 unsigned em2 = __ballot_sync(FULL, two);
                                 if (count_only) {
                                     my_count += (fin ? 1 : 0) + (two ? 1 : 0);
+                                } else if constexpr (DIRECT) {
+                                    const uint32_t cnt = __popc(em) + __popc(em2);
+                                    unsigned long long off = 0;
+                                    if (lane == 0)
+                                        off = atomicAdd(&L.ctl->pos, (unsigned long long)cnt);
+                                    off = __shfl_sync(FULL, off, 0);
+                                    if (fin) {
+                                        const uint32_t a = L.ix.orig[qpos], b = L.ix.orig[cpos];
+                                        const unsigned long long i1 = off + __popc(em & lt);
+                                        if (i1 < L.cap)
+                                            L.out[i1] = gj_pair{a, b};
+                                        if (two) {
+                                            const unsigned long long i2 = off + __popc(em) + __popc(em2 & lt);
+                                            if (i2 < L.cap)
+                                                L.out[i2] = gj_pair{b, a};
+                                        }
+                                    }
                                 } else {
                                     uint32_t cnt = __popc(em) + __popc(em2);
                                     uint32_t off = 0;
@@ -274,7 +295,7 @@ __global__ void __launch_bounds__(JT) k_join_plain(JoinLaunch L)
                     }
                     __syncthreads();
                     // ---- commit when the staging area could not hold another tile
-                    if (!count_only && H.stg_cnt > flush_at) {
+                    if (staged && H.stg_cnt > flush_at) {
                         if (tid == 0) {
                             uint32_t cnt = H.stg_cnt;
                             unsigned long long b = atomicAdd(&L.ctl->pos, (unsigned long long)cnt);
@@ -303,7 +324,7 @@ __global__ void __launch_bounds__(JT) k_join_plain(JoinLaunch L)
         }
         __syncthreads();
         // ---- end of item: commit the rest, or defer from the first uncommitted tile
-        if (!count_only) {
+        if (staged) {
             if (tid == 0 && !H.stop) {
                 uint32_t cnt = H.stg_cnt;
                 H.ok = 1;
@@ -367,6 +388,27 @@ int plain_ctas_per_sm(int d)
 }
 
 size_t plain_smem_bytes(int d) { return plain_smem(d, plain_ct(d)); }
+
+cudaError_t launch_join_plain_direct(const JoinLaunch &L, int grid, cudaStream_t s)
+{
+    const int ct = plain_ct(L.ix.d);
+    const size_t sm = plain_smem(L.ix.d, ct);
+    cudaError_t e;
+    if (ct == 64) {
+        e = cudaFuncSetAttribute(k_join_plain<64, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess)
+            return e;
+        note_launch();
+        k_join_plain<64, true><<<grid, JT, sm, s>>>(L);
+    } else {
+        e = cudaFuncSetAttribute(k_join_plain<32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess)
+            return e;
+        note_launch();
+        k_join_plain<32, true><<<grid, JT, sm, s>>>(L);
+    }
+    return cudaGetLastError();
+}
 
 cudaError_t launch_join_plain(const JoinLaunch &L, int grid, cudaStream_t s)
 {

@@ -64,7 +64,7 @@ class gj_join_stats(C.Structure):
 EXPORTS = ["gj_config_init", "gj_index_build", "gj_index_build_ex", "gj_self_join",
            "gj_self_join_part", "gj_index_get_info", "gj_last_join_stats", "gj_free",
            "gj_last_status", "gj_status_string", "gj_version", "gj_probe_fp64_tflops",
-           "gj_kernel_launches", "gj_debug_tc_tile"]
+           "gj_kernel_launches", "gj_debug_tc_tile", "gj_self_join_noalloc"]
 
 _lib = None
 
@@ -107,6 +107,8 @@ def load(path: str | None = None):
     lib.gj_kernel_launches.argtypes = []
     lib.gj_debug_tc_tile.restype = C.c_int
     lib.gj_debug_tc_tile.argtypes = [V, V, C.c_int32, V]
+    lib.gj_self_join_noalloc.restype = C.c_int
+    lib.gj_self_join_noalloc.argtypes = [V, C.c_int32, C.c_int32, V, C.c_uint64, C.POINTER(C.c_uint64)]
     if path is None:
         _lib = lib
     return lib
@@ -193,6 +195,15 @@ def gj_self_join_part(h: int, part: int, nparts: int, out=None) -> tuple[int, in
     p, cap, keep = _ptr_pairs(out)
     cnt = C.c_uint64(0)
     st = load().gj_self_join_part(h, int(part), int(nparts), p, cap, C.byref(cnt))
+    del keep
+    return st, int(cnt.value)
+
+
+def gj_self_join_noalloc(h: int, out=None, part: int = 0, nparts: int = 1) -> tuple[int, int]:
+    """The allocation-free join into a device buffer; returns (status, |R|)."""
+    p, cap, keep = _ptr_pairs(out)
+    cnt = C.c_uint64(0)
+    st = load().gj_self_join_noalloc(h, int(part), int(nparts), p, cap, C.byref(cnt))
     del keep
     return st, int(cnt.value)
 
