@@ -83,6 +83,8 @@ struct TcShared {
     unsigned long long base;
     uint32_t sq[8][TC_SQ];   // per epilogue warp: survivors waiting for the FP64 recheck
     uint32_t sc[8][TC_SQ];
+    unsigned long long surv;     // survivors (statistics)
+    unsigned long long counted;  // pairs counted (count-only launches)
 };
 
 struct TcLaunch {
@@ -203,6 +205,67 @@ __device__ __noinline__ void tc_flush_survivors(const TcLaunch *__restrict__ T, 
     }
 }
 
+// Minimum of 32 values as signed integers (fp32 bit patterns), as a tree of
+// three-input minima: 16 operations, dependency depth 4.
+__device__ __forceinline__ int min32_tree(const uint32_t (&v)[32])
+{
+    int t[11];
+#pragma unroll
+    for (int i = 0; i < 10; ++i)
+        t[i] = __vimin3_s32((int)v[3 * i], (int)v[3 * i + 1], (int)v[3 * i + 2]);
+    t[10] = min((int)v[30], (int)v[31]);
+    const int u0 = __vimin3_s32(t[0], t[1], t[2]);
+    const int u1 = __vimin3_s32(t[3], t[4], t[5]);
+    const int u2 = __vimin3_s32(t[6], t[7], t[8]);
+    const int u3 = min(t[9], t[10]);
+    return min(__vimin3_s32(u0, u1, u2), u3);
+}
+
+// Rare path of the epilogue: some value of this 32-column chunk is <= T.
+// Re-reads the chunk from TMEM (the warp is converged here) and queues every
+// valid survivor, warp-aggregated; flushes the queue when it would overflow.
+__device__ __noinline__ uint32_t tc_queue_chunk(const TcLaunch *__restrict__ T, uint32_t taddr, uint32_t col0,
+                                                bool rvalid, uint32_t qpos, const TileDesc *__restrict__ D, int Tb,
+                                                uint32_t *sq, uint32_t *sc, uint32_t nq, gj_pair *stg,
+                                                uint32_t *cnt, uint32_t *flush_req,
+                                                unsigned long long *surv_sh, unsigned long long *counted_sh)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    uint32_t v[32];
+    tmem_ld32(taddr, v);
+    tmem_wait_ld();
+    const uint32_t r0 = D->r0, ws = D->ws, we = D->we;
+    const bool self = (D->flags & F_SELF) != 0;
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+        const uint32_t cpos = r0 + col0 + (uint32_t)i;
+        const bool h = rvalid && (int)v[i] <= Tb && cpos >= ws && cpos < we && (!self || cpos >= qpos);
+        const unsigned bal = __ballot_sync(0xffffffffu, h);
+        if (bal) {
+            const uint32_t k = (uint32_t)__popc(bal);
+            if (nq + k > (uint32_t)TC_SQ) {
+                unsigned long long c = 0;
+                __syncwarp();
+                tc_flush_survivors(T, sq, sc, nq, stg, cnt, flush_req, &c);
+                __syncwarp();
+                if (c)
+                    atomicAdd(counted_sh, c);
+                nq = 0;
+            }
+            if (h) {
+                const uint32_t at = nq + (uint32_t)__popc(bal & lt);
+                sq[at] = qpos;
+                sc[at] = cpos;
+            }
+            if (lane == 0)
+                atomicAdd(surv_sh, (unsigned long long)k);
+            nq += k;
+        }
+    }
+    return nq;
+}
+
 __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -231,6 +294,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
         S.flush_req = 0;
         S.half = 0;
         S.cnt[0] = S.cnt[1] = 0;
+        S.surv = 0;
+        S.counted = 0;
         fence_mbar_init();
     }
     if (warp == 1) {
@@ -337,7 +402,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
                         if (tile_idx < resume)
                             continue;
                         if (lane == 0) {
-                            if (!count_only && *(volatile unsigned int *)&L.ctl->full) {
+                            // another CTA filled the output: stop (polled every 32 tiles;
+                            // tiles made meanwhile are discarded by the failed commit)
+                            if (!count_only && (tile_idx & 31u) == 0 &&
+                                *(volatile unsigned int *)&L.ctl->full) {
                                 trunc = true;
                             } else {
                                 if (have) {
@@ -461,10 +529,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
         // ------------------------------------------------------------ epilogue
         const int e = warp - 2, q = warp & 3, hh = e >> 2;
         const int etid = threadIdx.x - 64;
-        const unsigned lt = (1u << lane) - 1u;
-        uint32_t turn = 0, es = 0, commit_tile = 0, nq = 0;
+        uint32_t turn = 0, es = 0, commit_tile = 0;
         bool failed = false, dead = false;
-        unsigned long long surv = 0, counted = 0, slots = 0;
+        unsigned long long slots = 0;
+        uint32_t *const sq = S.sq[e], *const sc = S.sc[e];
+        uint32_t nq = 0;
         const int Tb = T.Tbits;
         gj_pair *stg0 = count_only ? nullptr : L.staging + (size_t)blockIdx.x * 2 * TC_STG;
         // Cross-warp agreement only where a decision is needed: at the end of
@@ -499,48 +568,28 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
             const bool is_tile = !(D.flags & (F_MARKER | F_TERM));
             const uint32_t half = S.half;
             gj_pair *stg = stg0 ? stg0 + (size_t)half * TC_STG : nullptr;
-            uint32_t *const sq = S.sq[e], *const sc = S.sc[e];
             if (is_tile && !failed) {
                 const uint32_t row = (uint32_t)(hh * 128 + q * 32 + lane);
                 const uint32_t qpos = D.qa + row;
                 const bool rvalid = qpos >= D.qbeg && qpos < D.qbeg + D.qlen;
                 const uint32_t tb = tmem + ((uint32_t)(q * 32) << 16) + acc * 256u + (uint32_t)hh * 128u;
 #pragma unroll 1
-                for (int c = 0; c < 4; ++c) {
-                    uint32_t v[32];
-                    tmem_ld32(tb + (uint32_t)c * 32u, v);
+                for (int c2 = 0; c2 < 4; c2 += 2) {
+                    uint32_t va[32], vb[32];
+                    tmem_ld32(tb + (uint32_t)c2 * 32u, va);
+                    tmem_ld32(tb + (uint32_t)(c2 + 1) * 32u, vb);
                     tmem_wait_ld();
-                    int m = __vimin3_s32((int)v[0], (int)v[1], (int)v[2]);
-#pragma unroll
-                    for (int i = 3; i < 31; i += 2)
-                        m = __vimin3_s32(m, (int)v[i], (int)v[i + 1]);
-                    m = min(m, (int)v[31]);
-                    const bool hit = rvalid && m <= Tb;
-                    if (__any_sync(0xffffffffu, hit)) {
-                        // queue the chunk's survivors, column by column (warp-aggregated)
-#pragma unroll
-                        for (int i = 0; i < 32; ++i) {
-                            const uint32_t cpos = D.r0 + (uint32_t)(c * 32 + i);
-                            const bool h = hit && (int)v[i] <= Tb && cpos >= D.ws && cpos < D.we &&
-                                           (!(D.flags & F_SELF) || cpos >= qpos);
-                            const unsigned bal = __ballot_sync(0xffffffffu, h);
-                            if (bal) {
-                                const uint32_t k = (uint32_t)__popc(bal);
-                                if (nq + k > (uint32_t)TC_SQ) {
-                                    __syncwarp();
-                                    tc_flush_survivors(&T, sq, sc, nq, stg, &S.cnt[half], &S.flush_req, &counted);
-                                    __syncwarp();
-                                    nq = 0;
-                                }
-                                if (h) {
-                                    const uint32_t at = nq + (uint32_t)__popc(bal & lt);
-                                    sq[at] = qpos;
-                                    sc[at] = cpos;
-                                }
-                                nq += k;
-                                surv += h ? 1 : 0;
-                            }
-                        }
+                    const int ma = min32_tree(va), mb = min32_tree(vb);
+                    const bool ha = rvalid && ma <= Tb, hb = rvalid && mb <= Tb;
+                    if (__any_sync(0xffffffffu, ha || hb)) {
+                        if (__any_sync(0xffffffffu, ha))
+                            nq = tc_queue_chunk(&T, tb + (uint32_t)c2 * 32u, (uint32_t)c2 * 32u, rvalid, qpos,
+                                                &S.tdesc[acc], Tb, sq, sc, nq, stg, &S.cnt[half], &S.flush_req,
+                                                &S.surv, &S.counted);
+                        if (__any_sync(0xffffffffu, hb))
+                            nq = tc_queue_chunk(&T, tb + (uint32_t)(c2 + 1) * 32u, (uint32_t)(c2 + 1) * 32u, rvalid,
+                                                qpos, &S.tdesc[acc], Tb, sq, sc, nq, stg, &S.cnt[half],
+                                                &S.flush_req, &S.surv, &S.counted);
                     }
                 }
                 if (etid == 0) {
@@ -558,9 +607,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
             const bool item_end = (D.flags & (F_LAST | F_MARKER)) != 0;
             const bool flush = (D.flags & F_FLUSH) != 0;
             if (nq >= 32u || ((item_end || flush || (D.flags & F_TERM)) && nq)) {
+                unsigned long long c = 0;
                 __syncwarp();
-                tc_flush_survivors(&T, sq, sc, nq, stg, &S.cnt[half], &S.flush_req, &counted);
+                tc_flush_survivors(&T, sq, sc, nq, stg, &S.cnt[half], &S.flush_req, &c);
                 __syncwarp();
+                if (c)
+                    atomicAdd(&S.counted, c);
                 nq = 0;
             }
             if (D.flags & F_TERM)
@@ -622,21 +674,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
             S.abort = 1;
             atomicOr(&L.ctl->err, kErrTimeout);
         }
-        for (int o = 16; o; o >>= 1) {
-            surv += __shfl_xor_sync(0xffffffffu, surv, o);
-            counted += __shfl_xor_sync(0xffffffffu, counted, o);
-        }
-        if (lane == 0) {
-            if (surv)
-                atomicAdd(&L.ctl->survivors, surv);
-            if (counted)
-                atomicAdd(&L.ctl->counted, counted);
-        }
         if (etid == 0 && slots)
             atomicAdd(&L.ctl->evaluated, slots);
     }
 
     __syncthreads();
+    if (threadIdx.x == 0) {
+        if (S.surv)
+            atomicAdd(&L.ctl->survivors, S.surv);
+        if (S.counted)
+            atomicAdd(&L.ctl->counted, S.counted);
+    }
     if (S.abort) {
         // let copies and MMAs already issued land before the memory goes away
         const uint64_t t0 = globaltimer();
