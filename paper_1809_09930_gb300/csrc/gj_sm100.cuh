@@ -60,21 +60,32 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
 }
 
 // Wait for the phase with the given parity, for at most `limit_ns`.  Returns
-// false on timeout or when *abort becomes non-zero.
+// false on timeout or when *abort becomes non-zero.  The clock and the abort
+// flag are read every 256 polls only (reading %globaltimer is not free).
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile uint32_t *abort,
                                           uint64_t limit_ns)
 {
     if (mbar_try_wait(bar, parity))
         return true;
     const uint64_t t0 = globaltimer();
-    for (;;) {
+    for (uint32_t it = 1;; ++it) {
         if (mbar_try_wait(bar, parity))
             return true;
-        if (*abort)
-            return false;
-        if (globaltimer() - t0 > limit_ns)
-            return false;
+        if ((it & 255u) == 0) {
+            if (*abort)
+                return false;
+            if (globaltimer() - t0 > limit_ns)
+                return false;
+        }
     }
+}
+
+// min(a, b, c) of three fp32 values in one instruction (sm_100 family)
+__device__ __forceinline__ float fmin3(float a, float b, float c)
+{
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
 }
 
 // ---- bulk asynchronous copy global -> shared (16-byte aligned, size % 16 == 0)

@@ -205,20 +205,19 @@ __device__ __noinline__ void tc_flush_survivors(const TcLaunch *__restrict__ T, 
     }
 }
 
-// Minimum of 32 values as signed integers (fp32 bit patterns), as a tree of
-// three-input minima: 16 operations, dependency depth 4.
-__device__ __forceinline__ int min32_tree(const uint32_t (&v)[32])
+// Minimum of 32 fp32 values as a tree of three-input minima: 16 operations,
+// dependency depth 4.
+__device__ __forceinline__ float min32_tree(const uint32_t (&v)[32])
 {
-    int t[11];
+    float t[11];
 #pragma unroll
     for (int i = 0; i < 10; ++i)
-        t[i] = __vimin3_s32((int)v[3 * i], (int)v[3 * i + 1], (int)v[3 * i + 2]);
-    t[10] = min((int)v[30], (int)v[31]);
-    const int u0 = __vimin3_s32(t[0], t[1], t[2]);
-    const int u1 = __vimin3_s32(t[3], t[4], t[5]);
-    const int u2 = __vimin3_s32(t[6], t[7], t[8]);
-    const int u3 = min(t[9], t[10]);
-    return min(__vimin3_s32(u0, u1, u2), u3);
+        t[i] = fmin3(__uint_as_float(v[3 * i]), __uint_as_float(v[3 * i + 1]), __uint_as_float(v[3 * i + 2]));
+    t[10] = fminf(__uint_as_float(v[30]), __uint_as_float(v[31]));
+    const float u0 = fmin3(t[0], t[1], t[2]);
+    const float u1 = fmin3(t[3], t[4], t[5]);
+    const float u2 = fmin3(t[6], t[7], t[8]);
+    return fmin3(fmin3(u0, u1, u2), t[9], t[10]);
 }
 
 // Rare path of the epilogue: some value of this 32-column chunk is <= T.
@@ -535,6 +534,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
         uint32_t *const sq = S.sq[e], *const sc = S.sc[e];
         uint32_t nq = 0;
         const int Tb = T.Tbits;
+        const float Tf = __int_as_float(T.Tbits);
         gj_pair *stg0 = count_only ? nullptr : L.staging + (size_t)blockIdx.x * 2 * TC_STG;
         // Cross-warp agreement only where a decision is needed: at the end of
         // an item and when the MMA thread flags a flush in the descriptor (a
@@ -579,8 +579,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
                     tmem_ld32(tb + (uint32_t)c2 * 32u, va);
                     tmem_ld32(tb + (uint32_t)(c2 + 1) * 32u, vb);
                     tmem_wait_ld();
-                    const int ma = min32_tree(va), mb = min32_tree(vb);
-                    const bool ha = rvalid && ma <= Tb, hb = rvalid && mb <= Tb;
+                    const float ma = min32_tree(va), mb = min32_tree(vb);
+                    const bool ha = rvalid && ma <= Tf, hb = rvalid && mb <= Tf;
                     if (__any_sync(0xffffffffu, ha || hb)) {
                         if (__any_sync(0xffffffffu, ha))
                             nq = tc_queue_chunk(&T, tb + (uint32_t)c2 * 32u, (uint32_t)c2 * 32u, rvalid, qpos,
