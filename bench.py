@@ -47,7 +47,11 @@ def parse():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--form", choices=["plain", "tc"], default="plain")
+    ap.add_argument("--form", choices=["plain", "tc"], default="tc")
+    ap.add_argument("--workload", choices=["paper", "jobs"], default="paper",
+                    help="paper: 2M uniform points per d; jobs: the 256 uneven jobs in one launch")
+    ap.add_argument("--no-plain", action="store_true",
+                    help="skip the one-shot plain FP64 join of the d=16 set beside the tc form")
     ap.add_argument("--dims", default=None, help="comma list of d for the paper-scale workload")
     ap.add_argument("--n", type=int, default=2_000_000)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
@@ -178,8 +182,124 @@ def reference_arm(args, runs):
     print(json.dumps(out), flush=True)
 
 
+def plain_leg(gj, torch, data, col, fp64_tflops, stream):
+    """One plain FP64 join (SHORTC, no tensor cores) of the d=16 set, timed by
+    the library's CUDA events, with its FP64-pipe roofline fraction."""
+    for r, X, Xd in data:
+        if r["d"] != 16:
+            continue
+        with gj.Index(Xd[:50_000], r["eps"], k=0, stream=stream.cuda_stream) as w:
+            w.count()                                        # load the kernel
+        with gj.Index(Xd, r["eps"], k=0, stream=stream.cuda_stream) as ix:
+            info = ix.info()
+            st, cnt = gj.gj_self_join(ix.h, col["out"][16])
+            if st != gj.GJ_OK:
+                raise RuntimeError(f"plain join failed: {gj.gj_status_string(st)}")
+            s = ix.stats()
+        join_s = s["join_ms"] * 1e-3
+        achieved = 3.0 * s["dims"] / join_s / 1e12
+        peak = 0.75 * fp64_tflops
+        out = {"workload": f"d=16 set, n={r['n']}", "join_s": join_s, "pairs": cnt,
+               "evals_per_s": info["candidate_pairs"] / join_s,
+               "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                            "frac": achieved / peak, "kernel": "k_join_plain",
+                            "peak_source": "FP64 FMA probe measured in this run x 3/4 (DADD+DFMA mix)"}}
+        if cnt != col["pairs"].get(16):
+            out["mismatch"] = f"plain found {cnt} pairs, tc {col['pairs'].get(16)}"
+        return out
+    return None
+
+
+def bench_jobs(args):
+    """The many-jobs workload: 256 independent self-joins (n log-uniform in
+    [1k, 200k], d in {16, 18, 32}, uniform and mixture data alternating, eps per
+    job for 8-128 mean neighbours) built and joined in one persistent,
+    graph-captured launch.  Step = gj_batch_build + gj_batch_self_join."""
+    import torch
+    from paper_1809_09930_gb300 import gj
+    with open(WORKLOADS) as f:
+        specs = json.load(f)["jobs"]
+    steps = args.steps if args.steps is not None else 5
+    stream = torch.cuda.current_stream()
+    jobs = []
+    for js in specs:
+        X = synth.generate(js["kind"], js["n"], js["d"], js["seed"])
+        jobs.append((torch.from_numpy(X).cuda(), js["eps"], 0))
+    torch.cuda.synchronize()
+    cfg = gj.gj_config_init()
+    cfg.stream = stream.cuda_stream
+    # per-job candidate pairs (the unit) and contraction work, outside the timing
+    flops = 0.0
+    for (X, eps, _), js in zip(jobs, specs):
+        with gj.Index(X, eps, k=0, flags=gj.GJ_DEFAULT_FLAGS | gj.GJ_TC_FILTER) as ix:
+            flops += 2.0 * js["d"] * ix.info()["candidate_pairs"]
+    b = gj.gj_batch_build(jobs, cfg)
+    info = gj.gj_batch_get_info(b)
+    st, counts = gj.gj_batch_self_join(b, len(jobs))
+    outs = [torch.empty((c + 16, 2), dtype=torch.int32, device="cuda") for c in counts]
+    gj.gj_batch_free(b)
+
+    def step():
+        bb = gj.gj_batch_build(jobs, cfg)
+        st, c = gj.gj_batch_self_join(bb, len(jobs), outs)
+        if st != gj.GJ_OK or c != counts:
+            raise RuntimeError(f"batch join: {gj.gj_status_string(st)}")
+        return bb
+
+    for _ in range(args.warmup):
+        gj.gj_batch_free(step())
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.synchronize()
+    clocks.start()
+    l0 = gj.gj_kernel_launches()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    handles = []
+    for _ in range(steps):
+        handles.append(step())
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    launches = gj.gj_kernel_launches() - l0
+    ms = ev0.elapsed_time(ev1)
+    # the join alone: replay of the captured graph on the last batch
+    bb = handles[-1]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 5
+    e0.record(stream)
+    for _ in range(reps):
+        gj.gj_batch_self_join(bb, len(jobs), outs)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    join_ms = e0.elapsed_time(e1) / reps
+    for h in handles:
+        gj.gj_batch_free(h)
+    with open(PEAKS) as f:
+        pk = json.load(f)
+    peak = pk.get("bf16_tflops_sustained") or pk.get("bf16_tflops")
+    achieved = flops / (join_ms * 1e-3) / 1e12
+    evals = info["candidate_pairs"]
+    out = {
+        "metric": "distance evals/s (self-join, exact pair set)",
+        "value": evals * steps / (ms * 1e-3), "unit": "distance evals/s", "n_gpus": 1, "steps": steps,
+        "warmup": args.warmup, "ms_per_step": ms / steps, "higher_is_better": True, "scaling": "strong",
+        "vs_baseline": None, "dtype": "f16xf16->f32 filter + f64 recheck", "data": "synthetic",
+        "config": {"workload": f"{len(jobs)} independent self-joins in one launch, {info['total_points']} points",
+                   "form": "tc-batch", "work_items": info["work_items"], "pairs": int(sum(counts)),
+                   "step": "gj_batch_build (all indices) + gj_batch_self_join (one graph-captured launch)"},
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None, "kernel": "k_join_tc (many-jobs)",
+                     "join_ms_graph_replay": join_ms},
+        "cpu_baseline": None, "e2e": None, "gpu_launches": int(launches), "clocks": clk,
+    }
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
+    if args.workload == "jobs" and args.impl == "ours":
+        bench_jobs(args)
+        return
     runs = workload(args)
     if args.impl == "reference":
         reference_arm(args, runs)
@@ -224,6 +344,7 @@ def main():
                 raise RuntimeError(f"join failed: {gj.gj_status_string(st)}")
             s = ix.stats()
             collect["join_ms"] += s["join_ms"]
+            collect["join_ms_d"][r["d"]] = collect["join_ms_d"].get(r["d"], 0.0) + s["join_ms"]
             collect["launches_join"] += s["launches"]
             collect["dims"] += s["dims"]
             collect["evaluated"] += s["evaluated"]
@@ -237,7 +358,7 @@ def main():
 
     def fresh():
         return {"cap": {}, "out": {}, "join_ms": 0.0, "launches_join": 0, "dims": 0, "evaluated": 0,
-                "pairs": {}, "k": {}, "flops": 0.0, "survivors": 0}
+                "pairs": {}, "k": {}, "flops": 0.0, "survivors": 0, "join_ms_d": {}}
 
     col = fresh()
     for _ in range(args.warmup):
@@ -330,6 +451,14 @@ def main():
         e2e = {"value": ev / e2e_s, "unit": "distance evals/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h}
 
+    # the plain FP64 form of the same d=16 join, once, for the TC-vs-plain ratio
+    plain = None
+    if args.form == "tc" and not args.no_plain and rank == 0 and world == 1:
+        plain = plain_leg(gj, torch, data, col, fp64_tflops, stream)
+        if plain and col["join_ms_d"].get(16):
+            # same join, same exact pair set: join time of the plain form over the tc form's
+            plain["tc_join_speedup"] = plain["join_s"] / (col["join_ms_d"][16] * 1e-3 / steps)
+
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -360,7 +489,9 @@ def main():
         "gpu_launches": int(launches),
         "clocks": clk,
         "join_stats": {"join_ms_total": col["join_ms"], "join_launches": col["launches_join"],
+                       "join_ms_per_step_by_d": {d: v / steps for d, v in col["join_ms_d"].items()},
                        "dims_evaluated": col["dims"], "pairs_evaluated": col["evaluated"]},
+        "plain_fp64": plain,
     }
     print(json.dumps(out), flush=True)
     if dist:

@@ -187,6 +187,51 @@ int gj_self_join_part(gj_index *h, int32_t part, int32_t nparts, gj_pair *pairs_
 int gj_self_join_noalloc(const gj_index *h, int32_t part, int32_t nparts, gj_pair *pairs_out,
                          uint64_t cap, uint64_t *count);
 
+/* ---- many independent self-joins in one launch (no paper counterpart) ---- */
+
+/* One job of a batched self-join: its own points (host or device, as for
+ * gj_index_build), size, dimension, search distance and k (0 = automatic). */
+typedef struct {
+    const double *points;
+    int64_t n;
+    int32_t d;
+    int32_t k;
+    double eps;
+} gj_job;
+
+typedef struct gj_batch gj_batch;
+
+/*
+ * Build the indices of njobs independent self-joins and combine them into one
+ * structure: points back to back (zero-padded to the largest d, which changes
+ * no distance), cells, adjacency and work items shifted per job, and one
+ * queue of every job's work items in descending estimated load.  All jobs use
+ * the tensor-core filter form (largest d at most 124).  cfg: device and
+ * stream as for gj_index_build_ex; flags REORDER/SORTIDU/SHORTC apply to
+ * every job.  Returns NULL with the reason in gj_last_status().
+ */
+gj_batch *gj_batch_build(const gj_job *jobs, int32_t njobs, const gj_config *cfg);
+
+/*
+ * Join every job in one persistent kernel launch.  The launch (parameter
+ * upload, counter reset, kernel, counter download) is captured in a CUDA graph
+ * on the first call and replayed on later calls.
+ *   outs[j]   device buffer of job j for caps[j] pairs (original row ids of
+ *             job j); NULL with caps[j] == 0 counts job j only.  outs and caps
+ *             may be NULL: count every job.
+ *   counts[j] out: |R_j|.
+ * Returns GJ_OK, or GJ_ERR_CAPACITY when some job's |R_j| exceeds caps[j]
+ * (that buffer then holds caps[j] pairs of R_j).
+ */
+int gj_batch_self_join(gj_batch *b, gj_pair *const *outs, const uint64_t *caps, uint64_t *counts);
+
+/* Work items, total points and the summed unordered candidate pairs of the
+ * jobs' grids (the unit of the distance-evaluation rate).  Any output may be NULL. */
+int gj_batch_get_info(const gj_batch *b, int64_t *work_items, int64_t *total_points, uint64_t *candidate_pairs);
+
+/* Release a batch.  NULL-safe. */
+void gj_batch_free(gj_batch *b);
+
 /* Facts about the index (k used, REORDER permutation, cell and candidate counts). */
 int gj_index_get_info(const gj_index *h, gj_index_info_t *info);
 

@@ -30,6 +30,7 @@ static thread_local int t_last_status = GJ_OK;
 static std::atomic<unsigned long long> g_launches{0};
 
 namespace gj {
+void set_last_status(int st) { t_last_status = st; }
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 unsigned long long launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
 }  // namespace gj
@@ -569,6 +570,7 @@ void gj_free(gj_index *h)
     cudaFree(h->order);
     cudaFree(h->XA);
     cudaFree(h->XB);
+    cudaFree(h->tc_centre);
     if (h->drain_stream)
         cudaStreamDestroy(h->drain_stream);
     if (h->own_stream && h->stream)

@@ -1,0 +1,452 @@
+// gj_batch.cu -- many independent self-joins in one persistent launch.
+//
+// No paper counterpart (the paper runs one self-join at a time).  Each job's
+// index is built with the single-job builder (REORDER, grid, adjacency, work
+// items, fp16 filter operands), then the jobs are concatenated into one
+// combined index:
+//   * points back to back in one FP64 structure-of-arrays, zero-padded to the
+//     largest d (a zero dimension adds exactly 0 to an FP64 running sum, so no
+//     distance decision changes);
+//   * cells, adjacency lists and work items shifted by each job's offsets,
+//     every work item tagged with its job;
+//   * the filter operands re-packed with one common K (each job keeps its own
+//     centre, scale and survivor threshold);
+//   * one queue of all work items in descending estimated load.
+// A join is then one launch of the tensor-core kernel in which every job
+// writes its pairs straight into its own device buffer through its own
+// counter.  The launch has no host decisions in it, so it is captured once in
+// a CUDA graph (parameter upload, counter reset, kernel, counter download) and
+// replayed on every later call.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "gj_internal.cuh"
+
+using namespace gj;
+
+struct gj_batch {
+    int device;
+    cudaStream_t stream;
+    bool own_stream;
+    int sms;
+    int32_t njobs;
+    int d_max, Kp;
+    int64_t n_total, npad, G_total, nitems;
+    double *X;
+    uint32_t *orig;
+    int64_t *cell_start, *adj_start;
+    uint32_t *adj;
+    Item *items;
+    uint32_t *order;
+    void *XA, *XB;
+    TcJob *jobs_dev;
+    TcJob *jobs_host;           // pinned: the launch parameters uploaded by the graph
+    unsigned long long *jpos;   // device counters
+    unsigned long long *jpos_host;   // pinned
+    JoinCtl *ctl;
+    cudaGraphExec_t graph;
+    bool graph_ready;
+    std::vector<uint64_t> n_job;
+    uint64_t candidates;        // sum over jobs of the unordered candidate pairs of the grid
+};
+
+namespace {
+
+__global__ void k_shift_i64(const int64_t *__restrict__ src, int64_t count, int64_t add, int64_t *__restrict__ dst)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < count)
+        dst[i] = src[i] + add;
+}
+
+__global__ void k_shift_u32(const uint32_t *__restrict__ src, int64_t count, uint32_t add, uint32_t *__restrict__ dst)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < count)
+        dst[i] = src[i] + add;
+}
+
+__global__ void k_shift_items(const Item *__restrict__ src, int64_t count, uint32_t cell_add, uint32_t pos_add,
+                              uint32_t job, Item *__restrict__ dst)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < count) {
+        Item it = src[i];
+        dst[i] = Item{it.cell + cell_add, it.qbeg + pos_add, it.qlen, job};
+    }
+}
+
+__global__ void k_set_one_i64(int64_t *p, int64_t v) { *p = v; }
+
+// key = ~float bits of the estimated load qlen * (points in the searched cells)
+__global__ void k_item_loads(const Item *__restrict__ items, int64_t nitems, const int64_t *__restrict__ cell_start,
+                             const int64_t *__restrict__ adj_start, const uint32_t *__restrict__ adj,
+                             uint64_t *__restrict__ key, uint32_t *__restrict__ val)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= nitems)
+        return;
+    const Item it = items[i];
+    int64_t pts = cell_start[it.cell + 1] - it.qbeg;
+    for (int64_t a = adj_start[it.cell]; a < adj_start[it.cell + 1]; ++a) {
+        const uint32_t b = adj[a];
+        if (b != it.cell)
+            pts += cell_start[b + 1] - cell_start[b];
+    }
+    const float load = (float)it.qlen * (float)pts;
+    key[i] = (uint64_t)(~__float_as_uint(load));
+    val[i] = (uint32_t)i;
+}
+
+int cuda_status(cudaError_t e)
+{
+    if (e == cudaSuccess)
+        return GJ_OK;
+    return e == cudaErrorMemoryAllocation ? GJ_ERR_OOM : GJ_ERR_CUDA;
+}
+
+int64_t blocks(int64_t n, int t) { return (n + t - 1) / t; }
+
+}  // namespace
+
+extern "C" {
+
+void gj_batch_free(gj_batch *b)
+{
+    if (!b)
+        return;
+    cudaSetDevice(b->device);
+    if (b->stream)
+        cudaStreamSynchronize(b->stream);
+    if (b->graph_ready)
+        cudaGraphExecDestroy(b->graph);
+    cudaFree(b->X);
+    cudaFree(b->orig);
+    cudaFree(b->cell_start);
+    cudaFree(b->adj_start);
+    cudaFree(b->adj);
+    cudaFree(b->items);
+    cudaFree(b->order);
+    cudaFree(b->XA);
+    cudaFree(b->XB);
+    cudaFree(b->jobs_dev);
+    cudaFreeHost(b->jobs_host);
+    cudaFree(b->jpos);
+    cudaFreeHost(b->jpos_host);
+    cudaFree(b->ctl);
+    if (b->own_stream && b->stream)
+        cudaStreamDestroy(b->stream);
+    delete b;
+}
+
+gj_batch *gj_batch_build(const gj_job *jobs, int32_t njobs, const gj_config *cfg_in)
+{
+    gj_config cfg;
+    if (cfg_in)
+        cfg = *cfg_in;
+    else
+        gj_config_init(&cfg);
+    if (!jobs || njobs < 1) {
+        gj::set_last_status(GJ_ERR_INVALID_ARG);
+        return nullptr;
+    }
+    int d_max = 1;
+    int64_t n_total = 0;
+    for (int32_t j = 0; j < njobs; ++j) {
+        if (jobs[j].d < 1 || jobs[j].n < 0 || !(jobs[j].eps > 0.0)) {
+            gj::set_last_status(GJ_ERR_INVALID_ARG);
+            return nullptr;
+        }
+        d_max = std::max(d_max, (int)jobs[j].d);
+        n_total += jobs[j].n;
+    }
+    const int Kp = ((d_max + 4 + 15) / 16) * 16;
+    if (Kp > 128 || n_total >= ((int64_t)1 << 31)) {
+        gj::set_last_status(GJ_ERR_TOO_LARGE);
+        return nullptr;
+    }
+    gj_batch *b = new (std::nothrow) gj_batch();
+    if (!b) {
+        gj::set_last_status(GJ_ERR_OOM);
+        return nullptr;
+    }
+    int st = GJ_OK;
+    cudaError_t e = cudaSuccess;
+    int dev = cfg.device;
+    if (dev < 0)
+        cudaGetDevice(&dev);
+    else
+        cudaSetDevice(dev);
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess || prop.major != 10 || prop.minor != 3) {
+        delete b;
+        gj::set_last_status(GJ_ERR_UNSUPPORTED);
+        return nullptr;
+    }
+    b->device = dev;
+    b->sms = prop.multiProcessorCount;
+    b->njobs = njobs;
+    b->d_max = d_max;
+    b->Kp = Kp;
+    b->n_total = n_total;
+    b->npad = ((n_total + 31) / 32) * 32 + 32;
+    if (cfg.stream) {
+        b->stream = (cudaStream_t)cfg.stream;
+    } else {
+        cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+        b->own_stream = true;
+    }
+    cudaStream_t s = b->stream;
+
+    // 1. per-job indices
+    std::vector<gj_index *> hs(njobs, nullptr);
+    gj_config jc = cfg;
+    jc.flags = cfg.flags | GJ_TC_FILTER;
+    jc.stream = (void *)s;
+    jc.device = dev;
+    int64_t G_total = 0, A_total = 0, I_total = 0;
+    for (int32_t j = 0; j < njobs && st == GJ_OK; ++j) {
+        jc.k = jobs[j].k;
+        hs[j] = gj_index_build_ex(jobs[j].points, jobs[j].n, jobs[j].d, jobs[j].eps, &jc);
+        if (!hs[j]) {
+            st = gj_last_status();
+            break;
+        }
+        G_total += hs[j]->G;
+        I_total += hs[j]->nitems;
+        b->candidates += hs[j]->info.candidate_pairs;
+    }
+    std::vector<int64_t> A_j(njobs, 0);
+    if (st == GJ_OK) {
+        for (int32_t j = 0; j < njobs; ++j) {
+            int64_t na = 0;
+            if (hs[j]->G > 0)
+                e = cudaMemcpyAsync(&na, hs[j]->adj_start + hs[j]->G, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess)
+                e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess)
+                break;
+            A_j[j] = na;
+            A_total += na;
+        }
+        st = cuda_status(e);
+    }
+    b->G_total = G_total;
+    b->nitems = I_total;
+    const size_t rows = (size_t)b->npad + 512;
+
+    // 2. combined arrays
+    uint64_t *k0 = nullptr, *k1 = nullptr;
+    uint32_t *v0 = nullptr, *v1 = nullptr, *counts = nullptr;
+    if (st == GJ_OK) {
+        e = cudaMalloc(&b->X, (size_t)d_max * b->npad * sizeof(double));
+        if (e == cudaSuccess) e = cudaMemsetAsync(b->X, 0, (size_t)d_max * b->npad * sizeof(double), s);
+        if (e == cudaSuccess) e = cudaMalloc(&b->orig, (size_t)b->npad * sizeof(uint32_t));
+        if (e == cudaSuccess) e = cudaMalloc(&b->cell_start, (size_t)(G_total + 1) * sizeof(int64_t));
+        if (e == cudaSuccess) e = cudaMalloc(&b->adj_start, (size_t)(G_total + 1) * sizeof(int64_t));
+        if (e == cudaSuccess) e = cudaMalloc(&b->adj, (size_t)std::max<int64_t>(A_total, 1) * sizeof(uint32_t));
+        if (e == cudaSuccess) e = cudaMalloc(&b->items, (size_t)std::max<int64_t>(I_total, 1) * sizeof(Item));
+        if (e == cudaSuccess) e = cudaMalloc(&b->order, (size_t)std::max<int64_t>(I_total, 1) * sizeof(uint32_t));
+        if (e == cudaSuccess) e = cudaMalloc(&b->XA, rows * Kp * 2);
+        if (e == cudaSuccess) e = cudaMalloc(&b->XB, rows * Kp * 2);
+        if (e == cudaSuccess) e = cudaMemsetAsync(b->XA, 0, rows * Kp * 2, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(b->XB, 0, rows * Kp * 2, s);
+        if (e == cudaSuccess) e = cudaMallocHost(&b->jobs_host, (size_t)njobs * sizeof(TcJob));
+        if (e == cudaSuccess) e = cudaMalloc(&b->jobs_dev, (size_t)njobs * sizeof(TcJob));
+        if (e == cudaSuccess) e = cudaMalloc(&b->jpos, (size_t)njobs * sizeof(unsigned long long));
+        if (e == cudaSuccess) e = cudaMallocHost(&b->jpos_host, (size_t)njobs * sizeof(unsigned long long));
+        if (e == cudaSuccess) e = cudaMalloc(&b->ctl, sizeof(JoinCtl));
+        st = cuda_status(e);
+    }
+    int64_t P = 0, C = 0, A = 0, I = 0;
+    for (int32_t j = 0; j < njobs && st == GJ_OK; ++j) {
+        gj_index *h = hs[j];
+        const int64_t n = h->info.n;
+        b->n_job.push_back((uint64_t)n);
+        if (n > 0) {
+            e = cudaMemcpy2DAsync(b->X + P, (size_t)b->npad * sizeof(double), h->X, (size_t)h->npad * sizeof(double),
+                                  (size_t)n * sizeof(double), (size_t)h->info.d, cudaMemcpyDeviceToDevice, s);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(b->orig + P, h->orig, (size_t)n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s);
+        }
+        if (e == cudaSuccess && h->G > 0) {
+            note_launch();
+            k_shift_i64<<<(int)blocks(h->G, 256), 256, 0, s>>>(h->cell_start, h->G, P, b->cell_start + C);
+            note_launch();
+            k_shift_i64<<<(int)blocks(h->G, 256), 256, 0, s>>>(h->adj_start, h->G, A, b->adj_start + C);
+            if (A_j[j] > 0) {
+                note_launch();
+                k_shift_u32<<<(int)blocks(A_j[j], 256), 256, 0, s>>>(h->adj, A_j[j], (uint32_t)C, b->adj + A);
+            }
+            if (h->nitems > 0) {
+                note_launch();
+                k_shift_items<<<(int)blocks(h->nitems, 256), 256, 0, s>>>(h->items, h->nitems, (uint32_t)C,
+                                                                          (uint32_t)P, (uint32_t)j, b->items + I);
+            }
+            e = cudaGetLastError();
+        }
+        // filter operands with the common K, this job's centre and scale
+        TcJob &J = b->jobs_host[j];
+        J.e2 = h->e2;
+        J.ew = h->ew;
+        J.u = h->u;
+        J.out = nullptr;
+        J.cap = 0;
+        if (e == cudaSuccess && h->tc_ready) {
+            e = tc_pack_into(h->X, n, h->npad, h->info.d, Kp, h->tc_sigma, h->tc_centre, P, b->XA, b->XB, s);
+            J.Tbits = tc_threshold_bits(h->info.eps, h->tc_sigma, h->tc_R0, h->info.d, Kp);
+        } else {
+            J.Tbits = 0;   // an empty job: nothing survives
+        }
+        if (e == cudaSuccess)
+            e = cudaStreamSynchronize(s);
+        st = cuda_status(e);
+        P += n;
+        C += h->G;
+        A += A_j[j];
+        I += h->nitems;
+    }
+    if (st == GJ_OK) {
+        note_launch();
+        k_set_one_i64<<<1, 1, 0, s>>>(b->cell_start + G_total, n_total);
+        note_launch();
+        k_set_one_i64<<<1, 1, 0, s>>>(b->adj_start + G_total, A_total);
+        e = cudaGetLastError();
+        st = cuda_status(e);
+    }
+    for (auto h : hs)
+        gj_free(h);
+
+    // 3. one queue of all work items by descending load
+    if (st == GJ_OK && I_total > 0) {
+        const int64_t ccap = radix_counts_needed(I_total);
+        e = cudaMalloc(&k0, I_total * sizeof(uint64_t));
+        if (e == cudaSuccess) e = cudaMalloc(&k1, I_total * sizeof(uint64_t));
+        if (e == cudaSuccess) e = cudaMalloc(&v0, I_total * sizeof(uint32_t));
+        if (e == cudaSuccess) e = cudaMalloc(&v1, I_total * sizeof(uint32_t));
+        if (e == cudaSuccess) e = cudaMalloc(&counts, ccap * sizeof(uint32_t));
+        if (e == cudaSuccess) {
+            note_launch();
+            k_item_loads<<<(int)blocks(I_total, 256), 256, 0, s>>>(b->items, I_total, b->cell_start, b->adj_start,
+                                                                   b->adj, k0, v0);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = radix_sort_pairs(k0, v0, k1, v1, I_total, 0, 32, counts, ccap, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(b->order, v0, I_total * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        st = cuda_status(e);
+    }
+    cudaFree(k0);
+    cudaFree(k1);
+    cudaFree(v0);
+    cudaFree(v1);
+    cudaFree(counts);
+    if (st != GJ_OK) {
+        gj_batch_free(b);
+        gj::set_last_status(st);
+        return nullptr;
+    }
+    gj::set_last_status(GJ_OK);
+    return b;
+}
+
+int gj_batch_self_join(gj_batch *b, gj_pair *const *outs, const uint64_t *caps, uint64_t *counts)
+{
+    if (!b || !counts)
+        return GJ_ERR_INVALID_ARG;
+    if (cudaSetDevice(b->device) != cudaSuccess)
+        return GJ_ERR_CUDA;
+    for (int32_t j = 0; j < b->njobs; ++j) {
+        gj_pair *o = outs ? outs[j] : nullptr;
+        const uint64_t c = caps ? caps[j] : 0;
+        if (!o && c > 0)
+            return GJ_ERR_INVALID_ARG;
+        if (o) {
+            cudaPointerAttributes a{};
+            if (cudaPointerGetAttributes(&a, o) != cudaSuccess) {
+                cudaGetLastError();
+                return GJ_ERR_INVALID_ARG;
+            }
+            if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)
+                return GJ_ERR_INVALID_ARG;
+        }
+        b->jobs_host[j].out = c ? o : nullptr;
+        b->jobs_host[j].cap = c;
+    }
+    cudaStream_t s = b->stream;
+    cudaError_t e = cudaSuccess;
+    if (!b->graph_ready) {
+        JoinLaunch L{};
+        L.ix.X = b->X;
+        L.ix.orig = b->orig;
+        L.ix.cell_start = b->cell_start;
+        L.ix.adj_start = b->adj_start;
+        L.ix.adj = b->adj;
+        L.ix.items = b->items;
+        L.ix.n = b->n_total;
+        L.ix.npad = b->npad;
+        L.ix.d = b->d_max;
+        L.ix.u = -1;
+        L.queue = b->order;
+        L.qlimit = (uint32_t)b->nitems;
+        L.ctl = b->ctl;
+        L.out = nullptr;   // pairs go to the jobs' own buffers
+        cudaGraph_t g = nullptr;
+        e = tc_jobs_launch_attr(b->Kp);
+        if (e == cudaSuccess)
+            e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaMemcpyAsync(b->jobs_dev, b->jobs_host, (size_t)b->njobs * sizeof(TcJob), cudaMemcpyHostToDevice, s);
+            cudaMemsetAsync(b->jpos, 0, (size_t)b->njobs * sizeof(unsigned long long), s);
+            cudaMemsetAsync(b->ctl, 0, sizeof(JoinCtl), s);
+            if (b->nitems > 0)
+                launch_join_tc_jobs(L, b->XA, b->XB, b->Kp, b->jobs_dev, b->jpos, b->sms, s);
+            cudaMemcpyAsync(b->jpos_host, b->jpos, (size_t)b->njobs * sizeof(unsigned long long),
+                            cudaMemcpyDeviceToHost, s);
+            e = cudaStreamEndCapture(s, &g);
+        }
+        if (e == cudaSuccess)
+            e = cudaGraphInstantiate(&b->graph, g, 0);
+        if (g)
+            cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return cuda_status(e);
+        }
+        b->graph_ready = true;
+    }
+    e = cudaGraphLaunch(b->graph, s);
+    if (b->nitems > 0)
+        note_launch();   // the graph's join kernel
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess)
+        return cuda_status(e);
+    bool over = false;
+    for (int32_t j = 0; j < b->njobs; ++j) {
+        counts[j] = b->jpos_host[j];
+        if (counts[j] > (caps ? caps[j] : 0) && outs && outs[j])
+            over = true;
+    }
+    return over ? GJ_ERR_CAPACITY : GJ_OK;
+}
+
+int gj_batch_get_info(const gj_batch *b, int64_t *work_items, int64_t *total_points, uint64_t *candidate_pairs)
+{
+    if (!b)
+        return GJ_ERR_INVALID_ARG;
+    if (candidate_pairs)
+        *candidate_pairs = b->candidates;
+    if (work_items)
+        *work_items = b->nitems;
+    if (total_points)
+        *total_points = b->n_total;
+    return GJ_OK;
+}
+
+}  // extern "C"

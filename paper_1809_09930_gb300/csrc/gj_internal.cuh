@@ -25,7 +25,7 @@ namespace gj {
 
 constexpr int QB = 128;            // most points of a work item the plain kernel holds
 constexpr int QB_PLAIN = 120;      // query block of a plain-path index
-constexpr int QB_TC = 248;         // query block of a tensor-core index (256-row A tile from qbeg & ~7)
+constexpr int QB_TC = 120;         // query block of a tensor-core index (128-row A tile from qbeg & ~7)
 constexpr int MAXK = 8;            // most indexed dimensions
 
 struct Item {
@@ -122,10 +122,26 @@ int plain_ctas_per_sm(int d);
 size_t plain_smem_bytes(int d);
 cudaError_t launch_fp64_probe(double *out, int iters, int grid, cudaStream_t s);
 
+// Per-job parameters of a many-jobs launch (gj_batch.cu).
+struct TcJob {
+    double e2, ew;       // fl(eps^2), SORTIDU window half-width
+    int u;               // SORTIDU dimension or -1
+    int Tbits;           // fp32 bits of the job's survivor threshold
+    gj_pair *out;        // the job's device output (nullptr = count only)
+    unsigned long long cap;
+};
+
 // ---- tensor-core filter (gj_tc.cu) -----------------------------------------
 int tc_prepare(gj_index *h, const double *stats_host, const int *perm, cudaStream_t s);
 cudaError_t launch_join_tc(const gj_index *h, const JoinLaunch &L, int grid, cudaStream_t s);
 size_t tc_staging_pairs_per_cta();
+int tc_threshold_bits(double eps, double sigma, double R0, int d, int Kp);
+cudaError_t tc_pack_into(const double *X, int64_t n, int64_t npad, int d, int Kp, double sigma, const double *centre,
+                         int64_t row_off, void *XA, void *XB, cudaStream_t s);
+cudaError_t launch_join_tc_jobs(const JoinLaunch &L, const void *XA, const void *XB, int Kp, const TcJob *jobs,
+                                unsigned long long *jpos, int grid, cudaStream_t s);
+cudaError_t tc_jobs_launch_attr(int Kp);
+void set_last_status(int st);
 
 }  // namespace gj
 
@@ -160,4 +176,5 @@ struct gj_index {
     int tc_Kp;
     int tc_Tbits;        // fp32 bits of the survivor threshold (scaled units)
     double tc_sigma, tc_R0;
+    double *tc_centre;   // device, the filter's centre per reordered dimension
 };

@@ -19,19 +19,19 @@
 // truncating adder's bound).  Every pair of R therefore survives.
 //
 // Kernel (one persistent CTA per SM, 320 threads):
-//   warp 0   producer: takes work items (query blocks of <= 248 points), loads
-//            the item's 256-row A tile and each 128-row candidate tile with
+//   warp 0   producer: takes work items (query blocks of <= 120 points), loads
+//            the item's 128-row A tile and each 256-row candidate tile with
 //            bulk asynchronous copies (TMA) into a ring of shared-memory
 //            stages, and passes tile descriptors down a ring;
-//   warp 1   one thread issues tcgen05.mma (two M=128 x N=128 MMAs per K step,
-//            one per half of the query block) into a double-buffered TMEM
-//            accumulator (2 x 256 fp32 columns) and commits to mbarriers;
+//   warp 1   one thread issues tcgen05.mma (one M=128 x N=256 MMA per K step)
+//            into a double-buffered TMEM accumulator (2 x 256 fp32 columns)
+//            and commits to mbarriers;
 //   warps 2-9 epilogue: read the accumulators with tcgen05.ld, reduce each
-//            32-column chunk with 3-input integer minima (t >= 0 compares as
-//            its bit pattern; negative rounding residue compares below T), and
-//            recheck survivors in FP64; exact pairs go to a double-buffered
-//            per-CTA staging area committed to the output per item (same
-//            resume protocol as the plain kernel).
+//            32-column chunk with three-input fp32 minima, mark the values
+//            <= T in per-lane bit masks, release the accumulator, then queue
+//            the marked candidates and recheck them in FP64 in batches; exact
+//            pairs go to a double-buffered per-CTA staging area committed to
+//            the output per item (same resume protocol as the plain kernel).
 // Every wait is bounded (globaltimer); on timeout the CTA flags the error,
 // lets in-flight copies land, frees its TMEM and returns.
 #include <cuda_fp16.h>
@@ -51,8 +51,8 @@ namespace gj {
 using namespace sm100;
 
 constexpr int TC_THREADS = 320;
-constexpr int TC_N = 128;        // candidate rows per tile
-constexpr int TC_M = 256;        // query rows per A tile (two M=128 halves)
+constexpr int TC_N = 256;        // candidate rows per tile (one M=128 x N=256 MMA per K step)
+constexpr int TC_M = 128;        // query rows per A tile
 constexpr int TC_DR = 16;        // descriptor ring entries
 constexpr uint32_t TC_STG = 1u << 18;   // staging pairs per half per CTA (4 tiles of worst-case output)
 constexpr uint64_t TC_LIMIT_NS = 4000000000ull;   // 4 s per wait
@@ -89,6 +89,8 @@ struct TcShared {
 
 struct TcLaunch {
     JoinLaunch J;
+    const TcJob *jobs;           // many-jobs launch: per-job parameters (else nullptr)
+    unsigned long long *jpos;    // many-jobs launch: per-job pair counters
     const unsigned char *XA;
     const unsigned char *XB;
     int Kp;
@@ -158,13 +160,14 @@ __device__ __forceinline__ bool tc_exact(const double *__restrict__ X, int64_t n
 // exact pairs into the staging half (or count them).  Called by all 32 lanes.
 __device__ __noinline__ void tc_flush_survivors(const TcLaunch *__restrict__ T, const uint32_t *sq,
                                                 const uint32_t *sc, uint32_t n, gj_pair *stg, uint32_t *cnt,
-                                                uint32_t *flush_req, unsigned long long *counted)
+                                                uint32_t *flush_req, unsigned long long *counted, uint32_t job)
 {
     const int lane = threadIdx.x & 31;
     const double *__restrict__ X = T->J.ix.X;
     const int64_t npad = T->J.ix.npad;
     const int d = T->J.ix.d;
-    const long long e2bits = __double_as_longlong(T->J.ix.e2);
+    const TcJob *jp = T->jobs ? &T->jobs[job] : nullptr;
+    const long long e2bits = __double_as_longlong(jp ? jp->e2 : T->J.ix.e2);
     for (uint32_t base = 0; base < n; base += 32) {
         const uint32_t i = base + lane;
         bool keep = false;
@@ -175,7 +178,7 @@ __device__ __noinline__ void tc_flush_survivors(const TcLaunch *__restrict__ T, 
             keep = tc_exact(X, npad, d, e2bits, qpos, cpos);
         }
         const uint32_t np = keep ? ((qpos != cpos) ? 2u : 1u) : 0u;
-        if (stg == nullptr) {
+        if (stg == nullptr && jp == nullptr) {
             *counted += np;
             continue;
         }
@@ -186,12 +189,31 @@ __device__ __noinline__ void tc_flush_survivors(const TcLaunch *__restrict__ T, 
                 incl += y;
         }
         const uint32_t tot = __shfl_sync(0xffffffffu, incl, 31);
+        if (jp) {
+            // many-jobs launch: straight into the job's buffer (pairs past its
+            // capacity are counted, not written)
+            unsigned long long o64 = 0;
+            if (lane == 0 && tot)
+                o64 = atomicAdd(&T->jpos[job], (unsigned long long)tot);
+            o64 = __shfl_sync(0xffffffffu, o64, 0) + incl - np;
+            if (np && jp->out) {
+                const uint32_t a = T->J.ix.orig[qpos], b = T->J.ix.orig[cpos];
+                if (o64 < jp->cap)
+                    jp->out[o64] = gj_pair{a, b};
+                if (np == 2 && o64 + 1 < jp->cap)
+                    jp->out[o64 + 1] = gj_pair{b, a};
+            }
+            continue;
+        }
         uint32_t off = 0;
         if (lane == 0 && tot)
             off = atomicAdd(cnt, tot);
         off = __shfl_sync(0xffffffffu, off, 0) + incl - np;
         if (tot) {
-            if (off + np > TC_STG - 3u * 2u * 128u * 256u)
+            // soft limit: room for three more tiles of worst-case output (written
+            // before the accumulator is released) plus the small post-release
+            // output of up to four turns
+            if (off + np > TC_STG - 3u * 2u * 128u * 256u - 4096u)
                 *(volatile uint32_t *)flush_req = 1u;
             if (off + np > TC_STG) {
                 atomicOr(&T->J.ctl->err, kErrStaging);
@@ -220,48 +242,59 @@ __device__ __forceinline__ float min32_tree(const uint32_t (&v)[32])
     return fmin3(fmin3(u0, u1, u2), t[9], t[10]);
 }
 
-// Rare path of the epilogue: some value of this 32-column chunk is <= T.
-// Re-reads the chunk from TMEM (the warp is converged here) and queues every
-// valid survivor, warp-aggregated; flushes the queue when it would overflow.
-__device__ __noinline__ uint32_t tc_queue_chunk(const TcLaunch *__restrict__ T, uint32_t taddr, uint32_t col0,
-                                                bool rvalid, uint32_t qpos, const TileDesc *__restrict__ D, int Tb,
-                                                uint32_t *sq, uint32_t *sc, uint32_t nq, gj_pair *stg,
-                                                uint32_t *cnt, uint32_t *flush_req,
-                                                unsigned long long *surv_sh, unsigned long long *counted_sh)
+// Bit i of the result: v[i] <= T (this lane's row against column i of a chunk).
+__device__ __forceinline__ uint32_t hit_mask32(const uint32_t (&v)[32], float Tf)
+{
+    uint32_t m = 0;
+#pragma unroll
+    for (int i = 0; i < 32; ++i)
+        m |= (__uint_as_float(v[i]) <= Tf ? 1u : 0u) << i;
+    return m;
+}
+
+// Rare path of the epilogue, run after the accumulator is released: queue the
+// valid survivors marked in each lane's hit mask (warp-aggregated), flushing
+// the queue through the FP64 recheck when it would overflow.  Returns the new
+// queue length.
+__device__ __noinline__ uint32_t tc_queue_bits(const TcLaunch *__restrict__ T, uint32_t mask, uint32_t col0,
+                                               uint32_t qpos, uint32_t r0, uint32_t ws, uint32_t we, bool self,
+                                               uint32_t *sq, uint32_t *sc, uint32_t nq, gj_pair *stg, uint32_t *cnt,
+                                               uint32_t *flush_req, unsigned long long *surv_sh,
+                                               unsigned long long *counted_sh, uint32_t job)
 {
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
-    uint32_t v[32];
-    tmem_ld32(taddr, v);
-    tmem_wait_ld();
-    const uint32_t r0 = D->r0, ws = D->ws, we = D->we;
-    const bool self = (D->flags & F_SELF) != 0;
-#pragma unroll
-    for (int i = 0; i < 32; ++i) {
-        const uint32_t cpos = r0 + col0 + (uint32_t)i;
-        const bool h = rvalid && (int)v[i] <= Tb && cpos >= ws && cpos < we && (!self || cpos >= qpos);
+    uint32_t found = 0;
+    for (;;) {
+        const bool have = mask != 0u;
+        if (!__any_sync(0xffffffffu, have))
+            break;
+        const uint32_t cpos = r0 + col0 + (have ? (uint32_t)(__ffs(mask) - 1) : 0u);
+        mask &= mask - 1u;
+        const bool h = have && cpos >= ws && cpos < we && (!self || cpos >= qpos);
         const unsigned bal = __ballot_sync(0xffffffffu, h);
-        if (bal) {
-            const uint32_t k = (uint32_t)__popc(bal);
-            if (nq + k > (uint32_t)TC_SQ) {
-                unsigned long long c = 0;
-                __syncwarp();
-                tc_flush_survivors(T, sq, sc, nq, stg, cnt, flush_req, &c);
-                __syncwarp();
-                if (c)
-                    atomicAdd(counted_sh, c);
-                nq = 0;
-            }
-            if (h) {
-                const uint32_t at = nq + (uint32_t)__popc(bal & lt);
-                sq[at] = qpos;
-                sc[at] = cpos;
-            }
-            if (lane == 0)
-                atomicAdd(surv_sh, (unsigned long long)k);
-            nq += k;
+        if (!bal)
+            continue;
+        const uint32_t k = (uint32_t)__popc(bal);
+        if (nq + k > (uint32_t)TC_SQ) {
+            unsigned long long c = 0;
+            __syncwarp();
+            tc_flush_survivors(T, sq, sc, nq, stg, cnt, flush_req, &c, job);
+            __syncwarp();
+            if (c)
+                atomicAdd(counted_sh, c);   // each lane counted its own pairs
+            nq = 0;
         }
+        if (h) {
+            const uint32_t at = nq + (uint32_t)__popc(bal & lt);
+            sq[at] = qpos;
+            sc[at] = cpos;
+        }
+        nq += k;
+        found += k;
     }
+    if (lane == 0 && found)
+        atomicAdd(surv_sh, (unsigned long long)found);
     return nq;
 }
 
@@ -363,7 +396,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
             ++nitem;
             const int64_t cell_end = L.ix.cell_start[it.cell + 1];
             const int64_t nb_begin = L.ix.adj_start[it.cell], nb_end = L.ix.adj_start[it.cell + 1];
-            const int u = L.ix.u;
+            const uint32_t job = T.jobs ? it.pad : 0u;
+            const int u = T.jobs ? T.jobs[job].u : L.ix.u;
+            const double ew = T.jobs ? T.jobs[job].ew : L.ix.ew;
+            const uint32_t jtb = T.jobs ? (uint32_t)T.jobs[job].Tbits : (uint32_t)T.Tbits;
             double ulo = 0.0, uhi = 0.0;
             if (u >= 0) {
                 ulo = L.ix.X[(int64_t)u * L.ix.npad + it.qbeg];
@@ -386,8 +422,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
                     }
                     if (u >= 0) {
                         const double *U = L.ix.X + (int64_t)u * L.ix.npad;
-                        ws = tc_lower_u(U, ws, we, ulo, L.ix.ew);
-                        we = tc_upper_u(U, ws, we, uhi, L.ix.ew);
+                        ws = tc_lower_u(U, ws, we, ulo, ew);
+                        we = tc_upper_u(U, ws, we, uhi, ew);
                     }
                 }
                 const int nw = (int)min((int64_t)32, nb_end - nb0);
@@ -416,7 +452,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
                                 }
                                 pend = TileDesc{item, tile_idx, (bw == it.cell) ? F_SELF : 0u, 0u,
                                                 it.qbeg, it.qlen, qa, (uint32_t)r0,
-                                                (uint32_t)s0, (uint32_t)e0, 0u, 0u};
+                                                (uint32_t)s0, (uint32_t)e0, job, jtb};
                                 have = true;
                             }
                         }
@@ -435,7 +471,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
                 } else {
                     TileDesc M{item, first ? resume : 0u, F_MARKER | F_LAST | (first ? F_FIRST : 0u) |
                                                          (trunc ? F_TRUNC : 0u),
-                               0u, it.qbeg, it.qlen, qa, 0u, 0u, 0u, 0u, 0u};
+                               0u, it.qbeg, it.qlen, qa, 0u, 0u, 0u, job, jtb};
                     if (!push(M, false))
                         dead = true;
                 }
@@ -465,6 +501,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
             const uint32_t lbo = 128, sbo = (uint32_t)T.Kp * 16;
             const uint32_t a0 = smem_addr(Abuf), b0 = smem_addr(Bbuf);
             const int ksteps = T.Kp / 16;
+            // descriptors of buffer 0 / stage 0; an operand at byte offset o adds
+            // o >> 4 to the start-address field (shared addresses stay < 2^18)
+            const uint64_t adesc0 = desc_kmajor(a0, lbo, sbo), bdesc0 = desc_kmajor(b0, lbo, sbo);
             uint32_t seq = 0, turn = 0, nitem = 0, abuf = 0;
             bool dead = false;
             for (;;) {
@@ -493,13 +532,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
                 }
                 if (!(D.flags & (F_MARKER | F_TERM))) {
                     tc_fence_after();
-                    const uint32_t abase = a0 + abuf * T.a_bytes, bbase = b0 + stage * T.b_bytes;
-                    for (int h = 0; h < 2; ++h) {
-                        const uint32_t dcol = tmem + acc * 256u + (uint32_t)h * 128u;
-                        const uint32_t ah = abase + (uint32_t)h * (T.a_bytes / 2);
-                        for (int ks = 0; ks < ksteps; ++ks)
-                            mma_f16(dcol, desc_kmajor(ah + ks * 256u, lbo, sbo),
-                                    desc_kmajor(bbase + ks * 256u, lbo, sbo), idesc, ks > 0 ? 1u : 0u);
+                    const uint64_t ad = adesc0 + ((abuf * T.a_bytes) >> 4);
+                    const uint64_t bd = bdesc0 + ((stage * T.b_bytes) >> 4);
+                    {
+                        const uint32_t dcol = tmem + acc * 256u;
+                        mma_f16(dcol, ad, bd, idesc, 0u);
+                        for (int ks = 1; ks < ksteps; ++ks)
+                            mma_f16(dcol, ad + (uint64_t)(ks * 16), bd + (uint64_t)(ks * 16), idesc, 1u);
                     }
                     mma_commit(&S.empty_b[stage]);
                     if (D.flags & F_LAST)
@@ -533,8 +572,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
         unsigned long long slots = 0;
         uint32_t *const sq = S.sq[e], *const sc = S.sc[e];
         uint32_t nq = 0;
-        const int Tb = T.Tbits;
-        const float Tf = __int_as_float(T.Tbits);
+        const float Tf0 = __int_as_float(T.Tbits);
         gj_pair *stg0 = count_only ? nullptr : L.staging + (size_t)blockIdx.x * 2 * TC_STG;
         // Cross-warp agreement only where a decision is needed: at the end of
         // an item and when the MMA thread flags a flush in the descriptor (a
@@ -566,30 +604,45 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
                 failed = false;
             }
             const bool is_tile = !(D.flags & (F_MARKER | F_TERM));
+            const float Tf = T.jobs ? __uint_as_float(D.p3) : Tf0;
             const uint32_t half = S.half;
             gj_pair *stg = stg0 ? stg0 + (size_t)half * TC_STG : nullptr;
+            uint32_t hm0 = 0, hm1 = 0, hm2 = 0, hm3 = 0;   // per-lane hit masks of the 4 chunks
+            bool anyhit = false;
+            uint32_t qpos = 0;
             if (is_tile && !failed) {
-                const uint32_t row = (uint32_t)(hh * 128 + q * 32 + lane);
-                const uint32_t qpos = D.qa + row;
+                const uint32_t row = (uint32_t)(q * 32 + lane);
+                qpos = D.qa + row;
                 const bool rvalid = qpos >= D.qbeg && qpos < D.qbeg + D.qlen;
                 const uint32_t tb = tmem + ((uint32_t)(q * 32) << 16) + acc * 256u + (uint32_t)hh * 128u;
-#pragma unroll 1
-                for (int c2 = 0; c2 < 4; c2 += 2) {
+                {
                     uint32_t va[32], vb[32];
-                    tmem_ld32(tb + (uint32_t)c2 * 32u, va);
-                    tmem_ld32(tb + (uint32_t)(c2 + 1) * 32u, vb);
+                    tmem_ld32(tb, va);
+                    tmem_ld32(tb + 32u, vb);
                     tmem_wait_ld();
                     const float ma = min32_tree(va), mb = min32_tree(vb);
                     const bool ha = rvalid && ma <= Tf, hb = rvalid && mb <= Tf;
                     if (__any_sync(0xffffffffu, ha || hb)) {
-                        if (__any_sync(0xffffffffu, ha))
-                            nq = tc_queue_chunk(&T, tb + (uint32_t)c2 * 32u, (uint32_t)c2 * 32u, rvalid, qpos,
-                                                &S.tdesc[acc], Tb, sq, sc, nq, stg, &S.cnt[half], &S.flush_req,
-                                                &S.surv, &S.counted);
-                        if (__any_sync(0xffffffffu, hb))
-                            nq = tc_queue_chunk(&T, tb + (uint32_t)(c2 + 1) * 32u, (uint32_t)(c2 + 1) * 32u, rvalid,
-                                                qpos, &S.tdesc[acc], Tb, sq, sc, nq, stg, &S.cnt[half],
-                                                &S.flush_req, &S.surv, &S.counted);
+                        anyhit = true;
+                        if (ha)
+                            hm0 = hit_mask32(va, Tf);
+                        if (hb)
+                            hm1 = hit_mask32(vb, Tf);
+                    }
+                }
+                {
+                    uint32_t va[32], vb[32];
+                    tmem_ld32(tb + 64u, va);
+                    tmem_ld32(tb + 96u, vb);
+                    tmem_wait_ld();
+                    const float ma = min32_tree(va), mb = min32_tree(vb);
+                    const bool ha = rvalid && ma <= Tf, hb = rvalid && mb <= Tf;
+                    if (__any_sync(0xffffffffu, ha || hb)) {
+                        anyhit = true;
+                        if (ha)
+                            hm2 = hit_mask32(va, Tf);
+                        if (hb)
+                            hm3 = hit_mask32(vb, Tf);
                     }
                 }
                 if (etid == 0) {
@@ -597,10 +650,52 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
                     slots += (unsigned long long)D.qlen * (hi > lo ? hi - lo : 0u);
                 }
             }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0)
-                mbar_arrive(&S.tmem_empty[acc]);
+            // A warp with few hits queues them after releasing the accumulator.
+            // A warp with many (dense data) queues and rechecks them before, so
+            // that its staging output is seen by the flush logic in time.
+            bool early = false;
+            if (anyhit) {
+                const int hits =
+                    __reduce_add_sync(0xffffffffu, __popc(hm0) + __popc(hm1) + __popc(hm2) + __popc(hm3));
+                early = hits > 32;
+            }
+            if (!early) {
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0)
+                    mbar_arrive(&S.tmem_empty[acc]);
+            }
+            if (anyhit) {
+                const bool self = (D.flags & F_SELF) != 0;
+                const uint32_t cb = (uint32_t)hh * 128u;
+                if (__any_sync(0xffffffffu, hm0 != 0u))
+                    nq = tc_queue_bits(&T, hm0, cb + 0u, qpos, D.r0, D.ws, D.we, self, sq, sc, nq, stg, &S.cnt[half],
+                                       &S.flush_req, &S.surv, &S.counted, D.p2);
+                if (__any_sync(0xffffffffu, hm1 != 0u))
+                    nq = tc_queue_bits(&T, hm1, cb + 32u, qpos, D.r0, D.ws, D.we, self, sq, sc, nq, stg, &S.cnt[half],
+                                       &S.flush_req, &S.surv, &S.counted, D.p2);
+                if (__any_sync(0xffffffffu, hm2 != 0u))
+                    nq = tc_queue_bits(&T, hm2, cb + 64u, qpos, D.r0, D.ws, D.we, self, sq, sc, nq, stg, &S.cnt[half],
+                                       &S.flush_req, &S.surv, &S.counted, D.p2);
+                if (__any_sync(0xffffffffu, hm3 != 0u))
+                    nq = tc_queue_bits(&T, hm3, cb + 96u, qpos, D.r0, D.ws, D.we, self, sq, sc, nq, stg, &S.cnt[half],
+                                       &S.flush_req, &S.surv, &S.counted, D.p2);
+                if (early && nq) {
+                    unsigned long long c = 0;
+                    __syncwarp();
+                    tc_flush_survivors(&T, sq, sc, nq, stg, &S.cnt[half], &S.flush_req, &c, D.p2);
+                    __syncwarp();
+                    if (c)
+                        atomicAdd(&S.counted, c);
+                    nq = 0;
+                }
+            }
+            if (early) {
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0)
+                    mbar_arrive(&S.tmem_empty[acc]);
+            }
             ++turn;
             // the accumulator is released; recheck queued survivors now when the
             // queue is half full, or when the item's results must be complete
@@ -609,7 +704,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
             if (nq >= 32u || ((item_end || flush || (D.flags & F_TERM)) && nq)) {
                 unsigned long long c = 0;
                 __syncwarp();
-                tc_flush_survivors(&T, sq, sc, nq, stg, &S.cnt[half], &S.flush_req, &c);
+                tc_flush_survivors(&T, sq, sc, nq, stg, &S.cnt[half], &S.flush_req, &c, D.p2);
                 __syncwarp();
                 if (c)
                     atomicAdd(&S.counted, c);
@@ -704,6 +799,7 @@ struct TcPrepParams {
     int d, Kp;
     double sigma;
     const double *centre;   // device, reordered dims
+    int64_t row_off;        // output row of point 0 (many-jobs layouts)
 };
 
 __global__ void k_tc_radius(const double *__restrict__ X, int64_t n, int64_t npad, int d,
@@ -769,14 +865,15 @@ __global__ void k_tc_pack(const double *__restrict__ X, int64_t n, int64_t npad,
                 b[e] = zero;
             }
         }
-        const int64_t idx = ((p >> 3) * (Kp / 8) + kc) * 8 + (p & 7);   // in 16-byte units
+        const int64_t r = p + P.row_off;
+        const int64_t idx = ((r >> 3) * (Kp / 8) + kc) * 8 + (r & 7);   // in 16-byte units
         XA[idx] = *reinterpret_cast<const uint4 *>(a);
         XB[idx] = *reinterpret_cast<const uint4 *>(b);
     }
 }
 
 // Survivor threshold in scaled units (see the file header for the terms).
-static double tc_threshold(double eps, double sigma, double R0, int d, int Kp)
+double tc_threshold(double eps, double sigma, double R0, int d, int Kp)
 {
     const double sd = sqrt((double)d);
     const double Rh = sigma * R0 * (1.0 + ldexp(1.0, -10)) + sd * ldexp(1.0, -24);
@@ -836,14 +933,14 @@ int tc_prepare(gj_index *h, const double *stats_host, const int *perm, cudaStrea
     if (e == cudaSuccess)
         e = cudaMemsetAsync(h->XB, 0, bytes, s);
     if (e == cudaSuccess) {
-        TcPrepParams P{d, Kp, sigma, centre};
+        TcPrepParams P{d, Kp, sigma, centre, 0};
         note_launch();
         k_tc_pack<<<(int)((n + 127) / 128), 128, 0, s>>>(h->X, n, h->npad, P, (uint4 *)h->XA, (uint4 *)h->XB);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess)
         e = cudaStreamSynchronize(s);
-    cudaFree(centre);
+    h->tc_centre = centre;   // kept: a many-jobs layout re-packs from it
     cudaFree(rmax);
     if (e != cudaSuccess)
         return e == cudaErrorMemoryAllocation ? GJ_ERR_OOM : GJ_ERR_CUDA;
@@ -881,6 +978,58 @@ static int tc_stages(int Kp, uint32_t *a_bytes, uint32_t *b_bytes, uint32_t *off
 
 size_t tc_staging_pairs_per_cta() { return 2 * (size_t)TC_STG; }
 
+int tc_threshold_bits(double eps, double sigma, double R0, int d, int Kp)
+{
+    const double Td = tc_threshold(eps, sigma, R0, d, Kp);
+    float Tf = (float)Td;
+    if ((double)Tf < Td)
+        Tf = nextafterf(Tf, INFINITY);
+    int Tb;
+    memcpy(&Tb, &Tf, sizeof(Tb));
+    return Tb;
+}
+
+cudaError_t tc_pack_into(const double *X, int64_t n, int64_t npad, int d, int Kp, double sigma, const double *centre,
+                         int64_t row_off, void *XA, void *XB, cudaStream_t s)
+{
+    if (n <= 0)
+        return cudaSuccess;
+    TcPrepParams P{d, Kp, sigma, centre, row_off};
+    note_launch();
+    k_tc_pack<<<(int)((n + 127) / 128), 128, 0, s>>>(X, n, npad, P, (uint4 *)XA, (uint4 *)XB);
+    return cudaGetLastError();
+}
+
+cudaError_t tc_jobs_launch_attr(int Kp)
+{
+    uint32_t a, b, ob, os;
+    size_t sm = 0;
+    if (tc_stages(Kp, &a, &b, &ob, &os, &sm) < 2)
+        return cudaErrorInvalidValue;
+    return cudaFuncSetAttribute(k_join_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+}
+
+// (call tc_jobs_launch_attr first: this launcher sets no attribute, so it can
+// run inside a stream capture)
+cudaError_t launch_join_tc_jobs(const JoinLaunch &L, const void *XA, const void *XB, int Kp, const TcJob *jobs,
+                                unsigned long long *jpos, int grid, cudaStream_t s)
+{
+    TcLaunch T{};
+    T.J = L;
+    T.jobs = jobs;
+    T.jpos = jpos;
+    T.XA = (const unsigned char *)XA;
+    T.XB = (const unsigned char *)XB;
+    T.Kp = Kp;
+    T.Tbits = 0;
+    size_t sm = 0;
+    T.NS = tc_stages(T.Kp, &T.a_bytes, &T.b_bytes, &T.off_b, &T.off_s, &sm);
+    if (T.NS < 2)
+        return cudaErrorInvalidValue;
+    k_join_tc<<<grid, TC_THREADS, sm, s>>>(T);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_join_tc(const gj_index *h, const JoinLaunch &L, int grid, cudaStream_t s)
 {
     TcLaunch T{};
@@ -893,10 +1042,6 @@ cudaError_t launch_join_tc(const gj_index *h, const JoinLaunch &L, int grid, cud
     T.NS = tc_stages(T.Kp, &T.a_bytes, &T.b_bytes, &T.off_b, &T.off_s, &sm);
     if (T.NS < 2)
         return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(k_join_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess)
-        return e;
-    note_launch();
     k_join_tc<<<grid, TC_THREADS, sm, s>>>(T);
     return cudaGetLastError();
 }

@@ -46,6 +46,11 @@ class gj_config(C.Structure):
                 ("batch_pairs", C.c_uint64), ("device", C.c_int32), ("reserved", C.c_uint32 * 7)]
 
 
+class gj_job(C.Structure):
+    _fields_ = [("points", C.c_void_p), ("n", C.c_int64), ("d", C.c_int32), ("k", C.c_int32),
+                ("eps", C.c_double)]
+
+
 class gj_index_info_t(C.Structure):
     _fields_ = [("n", C.c_int64), ("d", C.c_int32), ("k", C.c_int32), ("eps", C.c_double),
                 ("nonempty_cells", C.c_int64), ("work_items", C.c_int64),
@@ -64,7 +69,8 @@ class gj_join_stats(C.Structure):
 EXPORTS = ["gj_config_init", "gj_index_build", "gj_index_build_ex", "gj_self_join",
            "gj_self_join_part", "gj_index_get_info", "gj_last_join_stats", "gj_free",
            "gj_last_status", "gj_status_string", "gj_version", "gj_probe_fp64_tflops",
-           "gj_kernel_launches", "gj_debug_tc_tile", "gj_self_join_noalloc"]
+           "gj_kernel_launches", "gj_debug_tc_tile", "gj_self_join_noalloc", "gj_batch_build",
+           "gj_batch_self_join", "gj_batch_get_info", "gj_batch_free"]
 
 _lib = None
 
@@ -108,6 +114,14 @@ def load(path: str | None = None):
     lib.gj_debug_tc_tile.restype = C.c_int
     lib.gj_debug_tc_tile.argtypes = [V, V, C.c_int32, V]
     lib.gj_self_join_noalloc.restype = C.c_int
+    lib.gj_batch_build.restype = V
+    lib.gj_batch_build.argtypes = [C.POINTER(gj_job), C.c_int32, C.POINTER(gj_config)]
+    lib.gj_batch_self_join.restype = C.c_int
+    lib.gj_batch_self_join.argtypes = [V, V, V, V]
+    lib.gj_batch_get_info.restype = C.c_int
+    lib.gj_batch_get_info.argtypes = [V, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_uint64)]
+    lib.gj_batch_free.restype = None
+    lib.gj_batch_free.argtypes = [V]
     lib.gj_self_join_noalloc.argtypes = [V, C.c_int32, C.c_int32, V, C.c_uint64, C.POINTER(C.c_uint64)]
     if path is None:
         _lib = lib
@@ -266,6 +280,55 @@ def gj_debug_tc_tile(A, B) -> np.ndarray:
     if st != GJ_OK:
         raise GJError(st, "gj_debug_tc_tile")
     return D
+
+
+def gj_batch_build(jobs, cfg: gj_config | None = None) -> int:
+    """jobs: list of (points, eps, k) with points as for gj_index_build."""
+    arr = (gj_job * len(jobs))()
+    keep = []
+    for i, (pts, eps, k) in enumerate(jobs):
+        p, n, d, kp = _ptr_points(pts)
+        keep.append(kp)
+        arr[i].points = p
+        arr[i].n = n
+        arr[i].d = d
+        arr[i].k = int(k)
+        arr[i].eps = float(eps)
+    cfg = cfg if cfg is not None else gj_config_init()
+    h = load().gj_batch_build(arr, len(jobs), C.byref(cfg))
+    del keep
+    if not h:
+        raise GJError(gj_last_status(), "gj_batch_build")
+    return h
+
+
+def gj_batch_self_join(b: int, njobs: int, outs=None) -> tuple[int, list[int]]:
+    """outs: None (count only) or a list of (cap, 2) int32 CUDA tensors / None."""
+    counts = (C.c_uint64 * njobs)()
+    if outs is None:
+        st = load().gj_batch_self_join(b, None, None, counts)
+    else:
+        ptrs = (C.c_void_p * njobs)()
+        caps = (C.c_uint64 * njobs)()
+        for j, o in enumerate(outs):
+            p, cap, _ = _ptr_pairs(o)
+            ptrs[j] = p
+            caps[j] = cap
+        st = load().gj_batch_self_join(b, ptrs, caps, counts)
+    return st, [int(c) for c in counts]
+
+
+def gj_batch_get_info(b: int) -> dict:
+    wi, tp, cp = C.c_int64(), C.c_int64(), C.c_uint64()
+    st = load().gj_batch_get_info(b, C.byref(wi), C.byref(tp), C.byref(cp))
+    if st != GJ_OK:
+        raise GJError(st, "gj_batch_get_info")
+    return {"work_items": wi.value, "total_points": tp.value, "candidate_pairs": cp.value}
+
+
+def gj_batch_free(b: int) -> None:
+    if b:
+        load().gj_batch_free(b)
 
 
 # ---------------------------------------------------------------------------
