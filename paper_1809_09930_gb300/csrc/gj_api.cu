@@ -37,14 +37,25 @@ unsigned long long launches_so_far() { return g_launches.load(std::memory_order_
 
 namespace {
 
-int cuda_status(cudaError_t e)
+// GJ_DEBUG=1 in the environment prints every CUDA failure the library maps
+// to a status code (call site and CUDA's error string) to stderr.
+bool debug_on()
+{
+    static const bool on = getenv("GJ_DEBUG") && getenv("GJ_DEBUG")[0] == '1';
+    return on;
+}
+
+int cuda_status_at(cudaError_t e, const char *where)
 {
     if (e == cudaSuccess)
         return GJ_OK;
+    if (debug_on())
+        fprintf(stderr, "gj: %s failed: %s (%d)\n", where, cudaGetErrorString(e), (int)e);
     if (e == cudaErrorMemoryAllocation)
         return GJ_ERR_OOM;
     return GJ_ERR_CUDA;
 }
+#define cuda_status(e) cuda_status_at((e), __func__)
 
 __global__ void k_gather_queue(const uint32_t *__restrict__ order, int part, int nparts, int64_t nq,
                                int64_t nb, uint32_t *__restrict__ q)
@@ -159,8 +170,11 @@ int run_launch(gj_index *h, JoinBuffers &B, JoinLaunch L, int grid, JoinCtl init
     cudaEventElapsedTime(&ms, B.ev_k0, B.ev_k1);
     *kernel_ms += ms;
     *result = *B.hctl_dn;
-    if (result->err & (kErrStaging | kErrDeferred))
+    if (result->err & (kErrStaging | kErrDeferred)) {
+        if (debug_on())
+            fprintf(stderr, "gj: join kernel reported error bits 0x%x\n", result->err);
         return GJ_ERR_CUDA;
+    }
     if (result->err & kErrTimeout)
         return GJ_ERR_TIMEOUT;
     return GJ_OK;
@@ -198,7 +212,7 @@ int join_impl(gj_index *h, int part, int nparts, gj_pair *pairs_out, uint64_t ca
     do {                                                            \
         cudaError_t _e = (x);                                       \
         if (_e != cudaSuccess)                                      \
-            return cuda_status(_e);                                 \
+            return cuda_status_at(_e, #x);                          \
     } while (0)
     TRYC(cudaMalloc(&B.ctl, sizeof(JoinCtl)));
     TRYC(cudaMallocHost(&B.hctl_up, sizeof(JoinCtl)));

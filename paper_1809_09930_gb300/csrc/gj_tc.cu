@@ -1042,6 +1042,10 @@ cudaError_t launch_join_tc(const gj_index *h, const JoinLaunch &L, int grid, cud
     T.NS = tc_stages(T.Kp, &T.a_bytes, &T.b_bytes, &T.off_b, &T.off_s, &sm);
     if (T.NS < 2)
         return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(k_join_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess)
+        return e;
+    note_launch();
     k_join_tc<<<grid, TC_THREADS, sm, s>>>(T);
     return cudaGetLastError();
 }
