@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-baseline", action="store_true", help="skip the CPU oracle leg")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="build with the analytic k instead of the autotuner's picks")
     return ap.parse_args()
 
 
@@ -182,15 +184,22 @@ def reference_arm(args, runs):
     print(json.dumps(out), flush=True)
 
 
-def plain_leg(gj, torch, data, col, fp64_tflops, stream):
+def plain_leg(gj, torch, data, col, fp64_tflops, stream, tune=True):
     """One plain FP64 join (SHORTC, no tensor cores) of the d=16 set, timed by
     the library's CUDA events, with its FP64-pipe roofline fraction."""
     for r, X, Xd in data:
         if r["d"] != 16:
             continue
-        with gj.Index(Xd[:50_000], r["eps"], k=0, stream=stream.cuda_stream) as w:
+        kw = {"k": 0}
+        t = None
+        if tune:
+            tcfg = gj.gj_config_init()
+            tcfg.stream = stream.cuda_stream
+            t = gj.gj_autotune(Xd, r["eps"], tcfg)
+            kw = {"k": t["k"], "query_block": t["query_block"], "tile": t["tile"]}
+        with gj.Index(Xd[:50_000], r["eps"], stream=stream.cuda_stream, **kw) as w:
             w.count()                                        # load the kernel
-        with gj.Index(Xd, r["eps"], k=0, stream=stream.cuda_stream) as ix:
+        with gj.Index(Xd, r["eps"], stream=stream.cuda_stream, **kw) as ix:
             info = ix.info()
             st, cnt = gj.gj_self_join(ix.h, col["out"][16])
             if st != gj.GJ_OK:
@@ -199,15 +208,43 @@ def plain_leg(gj, torch, data, col, fp64_tflops, stream):
         join_s = s["join_ms"] * 1e-3
         achieved = 3.0 * s["dims"] / join_s / 1e12
         peak = 0.75 * fp64_tflops
-        out = {"workload": f"d=16 set, n={r['n']}", "join_s": join_s, "pairs": cnt,
+        out = {"workload": f"d=16 set, n={r['n']}", "join_s": join_s, "pairs": cnt, "k": info["k"],
+               "tuned": {f: t[f] for f in ("k", "query_block", "tile", "trials")} if t else None,
                "evals_per_s": info["candidate_pairs"] / join_s,
                "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                             "frac": achieved / peak, "kernel": "k_join_plain",
                             "peak_source": "FP64 FMA probe measured in this run x 3/4 (DADD+DFMA mix)"}}
         if cnt != col["pairs"].get(16):
             out["mismatch"] = f"plain found {cnt} pairs, tc {col['pairs'].get(16)}"
+        out["sampled"] = plain_sampled(gj, data, col, stream, peak)
         return out
     return None
+
+
+def plain_sampled(gj, data, col, stream, peak, nparts=32):
+    """The plain FP64 join of the d = 32 and 64 sets would take minutes, so it
+    runs on one part of an entity partition (Sec. 6.2: load-ordered work items
+    dealt round-robin, a load-stratified 1/nparts sample, count only); its
+    kernel busy time (each CTA's start-to-exit time averaged over the grid) x
+    nparts estimates the whole join, beside the tensor-core form's measured
+    join time of the same set."""
+    res = {}
+    steps = max(1, col.get("steps", 1))
+    for r, X, Xd in data:
+        if r["d"] == 16:
+            continue
+        with gj.Index(Xd, r["eps"], k=0, stream=stream.cuda_stream) as ix:
+            st, cnt = gj.gj_self_join_part(ix.h, nparts // 2, nparts, None)
+            if st != gj.GJ_OK:
+                raise RuntimeError(f"plain sampled join failed: {gj.gj_status_string(st)}")
+            s = ix.stats()
+        est_s = s["busy_ms"] * 1e-3 * nparts
+        achieved = 3.0 * s["dims"] / (s["busy_ms"] * 1e-3) / 1e12
+        tc_s = col["join_ms_d"].get(r["d"], 0.0) * 1e-3 / steps
+        res[r["d"]] = {"part": f"{nparts // 2} of {nparts}", "join_s_est": est_s, "pairs_in_part": cnt,
+                       "fp64_frac": achieved / peak,
+                       "tc_join_speedup_est": est_s / tc_s if tc_s else None}
+    return res
 
 
 def bench_jobs(args):
@@ -228,13 +265,20 @@ def bench_jobs(args):
     torch.cuda.synchronize()
     cfg = gj.gj_config_init()
     cfg.stream = stream.cuda_stream
-    # per-job candidate pairs (the unit) and contraction work, outside the timing
-    flops = 0.0
-    for (X, eps, _), js in zip(jobs, specs):
-        with gj.Index(X, eps, k=0, flags=gj.GJ_DEFAULT_FLAGS | gj.GJ_TC_FILTER) as ix:
-            flops += 2.0 * js["d"] * ix.info()["candidate_pairs"]
+    if not args.no_tune:
+        cfg.flags = gj.GJ_DEFAULT_FLAGS | gj.GJ_AUTOTUNE
+    # the first build runs the autotuner's trials (per-job k); later builds of
+    # the same job list reuse its picks
+    t0 = time.perf_counter()
     b = gj.gj_batch_build(jobs, cfg)
+    tune_s = time.perf_counter() - t0
+    ks = gj.gj_batch_get_k(b, len(jobs))
     info = gj.gj_batch_get_info(b)
+    # per-job contraction work at the picked k, outside the timing
+    flops = 0.0
+    for (X, eps, _), js, k in zip(jobs, specs, ks):
+        with gj.Index(X, eps, k=k, flags=gj.GJ_DEFAULT_FLAGS | gj.GJ_TC_FILTER) as ix:
+            flops += 2.0 * js["d"] * ix.info()["candidate_pairs"]
     st, counts = gj.gj_batch_self_join(b, len(jobs))
     outs = [torch.empty((c + 16, 2), dtype=torch.int32, device="cuda") for c in counts]
     gj.gj_batch_free(b)
@@ -286,7 +330,9 @@ def bench_jobs(args):
         "vs_baseline": None, "dtype": "f16xf16->f32 filter + f64 recheck", "data": "synthetic",
         "config": {"workload": f"{len(jobs)} independent self-joins in one launch, {info['total_points']} points",
                    "form": "tc-batch", "work_items": info["work_items"], "pairs": int(sum(counts)),
-                   "step": "gj_batch_build (all indices) + gj_batch_self_join (one graph-captured launch)"},
+                   "step": "gj_batch_build (all indices) + gj_batch_self_join (one graph-captured launch)",
+                   "k_histogram": {k: ks.count(k) for k in sorted(set(ks))},
+                   "first_build_with_tuning_s": tune_s},
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": None, "kernel": "k_join_tc (many-jobs)",
                      "join_ms_graph_replay": join_ms},
@@ -328,10 +374,29 @@ def main():
         data.append((r, X, Xd))
     torch.cuda.synchronize()
 
+    # autotuner: k, query block and tile per d by timed trials, once, before
+    # the warm-up; every step then builds with the picks
+    tuned = {}
+    tune_s = 0.0
+    if not args.no_tune:
+        t0 = time.perf_counter()
+        for r, X, Xd in data:
+            tcfg = gj.gj_config_init()
+            tcfg.flags = flags
+            tcfg.stream = stream.cuda_stream
+            tuned[r["d"]] = gj.gj_autotune(Xd, r["eps"], tcfg)
+        tune_s = time.perf_counter() - t0
+
+    def settings(d):
+        t = tuned.get(d)
+        if not t:
+            return {"k": 0}
+        return {"k": t["k"], "query_block": t["query_block"], "tile": t["tile"]}
+
     def one_step(collect):
         tot_evals = 0
         for r, X, Xd in data:
-            ix = gj.Index(Xd, r["eps"], k=0, flags=flags, stream=stream.cuda_stream)
+            ix = gj.Index(Xd, r["eps"], flags=flags, stream=stream.cuda_stream, **settings(r["d"]))
             info = ix.info()
             cap = collect["cap"].get(r["d"])
             if cap is None:
@@ -426,7 +491,9 @@ def main():
         def e2e_step():
             ev = 0
             for (r, X, _), hx in zip(data, hin):
-                ix = gj.Index(hx, r["eps"], k=0, flags=flags)
+                t = tuned.get(r["d"])
+                ix = gj.Index(hx, r["eps"], flags=flags, batch_pairs=t["batch_pairs"] if t else 0,
+                              **settings(r["d"]))
                 info = ix.info()
                 st, cnt = gj.gj_self_join_part(ix.h, rank, world, hout[r["d"]])
                 if st != gj.GJ_OK:
@@ -454,7 +521,8 @@ def main():
     # the plain FP64 form of the same d=16 join, once, for the TC-vs-plain ratio
     plain = None
     if args.form == "tc" and not args.no_plain and rank == 0 and world == 1:
-        plain = plain_leg(gj, torch, data, col, fp64_tflops, stream)
+        col["steps"] = steps
+        plain = plain_leg(gj, torch, data, col, fp64_tflops, stream, tune=not args.no_tune)
         if plain and col["join_ms_d"].get(16):
             # same join, same exact pair set: join time of the plain form over the tc form's
             plain["tc_join_speedup"] = plain["join_s"] / (col["join_ms_d"][16] * 1e-3 / steps)
@@ -482,7 +550,10 @@ def main():
                    "form": args.form, "eps": {r["d"]: r["eps"] for r in runs}, "k": col["k"],
                    "pairs": col["pairs"], "parallelism": f"entity partition x{world}",
                    "l2": "inputs larger than L2 (>=256 MB per point set)",
-                   "step": "index build (REORDER, grid, adjacency, queue) + join into a device buffer"},
+                   "step": "index build (REORDER, grid, adjacency, queue) + join into a device buffer",
+                   "tuned": {d: {f: t[f] for f in ("k", "query_block", "tile", "batch_pairs", "trials")}
+                             for d, t in tuned.items()},
+                   "tune_s": tune_s},
         "roofline": roof,
         "cpu_baseline": cb,
         "e2e": e2e,

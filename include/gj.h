@@ -55,6 +55,8 @@ extern "C" {
 #define GJ_SORTIDU    (1u << 1)  /* Sec. 4.3: sort cells by one un-indexed dim, window search */
 #define GJ_SHORTC     (1u << 2)  /* Sec. 4.4: stop a distance once it exceeds eps^2          */
 #define GJ_TC_FILTER  (1u << 3)  /* tensor-core candidate filter + exact FP64 recheck (no paper counterpart) */
+#define GJ_AUTOTUNE   (1u << 4)  /* build: pick k, query block, tile and b_s by timed trials (gj_autotune) */
+#define GJ_TUNE_FORM  (1u << 5)  /* autotune: also try both forms (plain and GJ_TC_FILTER), keep the faster */
 #define GJ_DEFAULT_FLAGS (GJ_REORDER | GJ_SORTIDU | GJ_SHORTC)
 
 /* One result pair: original row indices of the two points. */
@@ -73,7 +75,11 @@ typedef struct {
     void    *stream;      /* cudaStream_t to run on; NULL = a stream the handle creates             */
     uint64_t batch_pairs; /* result batch size b_s in pairs; 0 = the rule of Sec. 3.2.2           */
     int32_t  device;      /* CUDA device ordinal; -1 = the calling thread's current device        */
-    uint32_t reserved[7];
+    int32_t  query_block; /* points per work item (query tile): 0 = default (120); 8..128, and
+                           * at most 120 with GJ_TC_FILTER (the 128-row tensor-core A tile)    */
+    int32_t  tile;        /* plain form: candidate points staged per shared-memory tile,
+                           * 0 = default (64 for d <= 32, else 32), 32 or 64                    */
+    uint32_t reserved[5];
 } gj_config;
 
 /* Read-only facts about a built index. */
@@ -104,6 +110,9 @@ typedef struct {
     double   join_ms;        /* device time of the join kernels (CUDA events)                   */
     double   estimate_ms;    /* device time of the sampled estimate                              */
     double   total_ms;       /* host wall time of the call                                       */
+    double   busy_ms;        /* join kernels: each CTA's start-to-exit time, averaged over the
+                              * CTAs of a launch, summed over launches (the join's work spread
+                              * evenly over the grid: its time without the tail)                  */
 } gj_join_stats;
 
 /* Fill *cfg with defaults (k = 0, GJ_DEFAULT_FLAGS, own stream, paper batch rule). */
@@ -128,6 +137,42 @@ void gj_config_init(gj_config *cfg);
 gj_index *gj_index_build(const double *points, int64_t n, int32_t d, double eps, int32_t k);
 gj_index *gj_index_build_ex(const double *points, int64_t n, int32_t d, double eps,
                             const gj_config *cfg);
+
+/* Choices of the autotuner for one input. */
+typedef struct {
+    int32_t  k;            /* indexed dimensions                                              */
+    uint32_t flags;        /* the input flags with GJ_TC_FILTER set or cleared by the pick     */
+    int32_t  query_block;  /* points per work item                                            */
+    int32_t  tile;         /* plain form: candidate tile (0 for the tensor-core form)         */
+    uint64_t batch_pairs;  /* result batch size b_s for host output                           */
+    uint64_t est_pairs;    /* |R| extrapolated from the trial join of the pick                */
+    double   build_ms;     /* device-synchronous host time of the pick's index build          */
+    double   join_ms;      /* join kernel time extrapolated from the pick's trial             */
+    int32_t  trials;       /* timed trials run                                                */
+    int32_t  reserved;
+} gj_tune_result;
+
+/*
+ * Autotuner (no paper counterpart; the paper fixes k by a comparison of
+ * candidate counts against index search cost, Sec. 4.1).  Picks k, the query
+ * block and the plain form's candidate tile by timed trials: for each
+ * candidate setting it builds the index and times a count-only join over a
+ * fixed, load-stratified share of the work items (one part of an entity
+ * partition, Sec. 6.2), extrapolated to the whole queue; the setting with the
+ * least build + join time wins.  k runs over 1..min(d, 8) (1..3 for the
+ * tensor-core form), the plain tiles over query blocks {120, 64} x candidate
+ * tiles {64, 32}.  With GJ_TUNE_FORM in cfg->flags both forms are tried,
+ * else only the form cfg->flags names.  The result batch size b_s is then
+ * chosen from the trial's |R| estimate, a timed device-to-host copy and the
+ * measured per-launch overhead, so that the drain of each batch hides under
+ * the join of the next (at least 3 batches, Sec. 3.2.2).
+ *   points, n, d, eps, cfg  as for gj_index_build_ex (cfg->k is ignored).
+ *   out     the pick.
+ * Returns GJ_OK or an error code.  Every trial runs on cfg's device and
+ * stream; nothing persists after the call.
+ */
+int gj_autotune(const double *points, int64_t n, int32_t d, double eps, const gj_config *cfg,
+                gj_tune_result *out);
 
 /*
  * The self-join (Alg. 1, batch loop and SelfJoinKernel): writes R into
@@ -211,6 +256,14 @@ typedef struct gj_batch gj_batch;
  * every job.  Returns NULL with the reason in gj_last_status().
  */
 gj_batch *gj_batch_build(const gj_job *jobs, int32_t njobs, const gj_config *cfg);
+/*
+ * With GJ_AUTOTUNE in cfg->flags, every job whose k is 0 gets its k from
+ * timed trials: the whole batch is built and joined (count only) once with
+ * every such job at k = 1, 2 and 3 (capped at its d), the kernel timing each
+ * job's work items on the SM clock, and each job keeps the k of its fastest
+ * trial.  The picks are remembered per process for the same list of job
+ * shapes (n, d, eps), so a later build of that list skips the trials.
+ */
 
 /*
  * Join every job in one persistent kernel launch.  The launch (parameter
@@ -228,6 +281,10 @@ int gj_batch_self_join(gj_batch *b, gj_pair *const *outs, const uint64_t *caps, 
 /* Work items, total points and the summed unordered candidate pairs of the
  * jobs' grids (the unit of the distance-evaluation rate).  Any output may be NULL. */
 int gj_batch_get_info(const gj_batch *b, int64_t *work_items, int64_t *total_points, uint64_t *candidate_pairs);
+
+/* The k each job's grid uses (k_per_job[j], njobs entries): the job's own k,
+ * or the autotuner's pick when the batch was built with GJ_AUTOTUNE. */
+int gj_batch_get_k(const gj_batch *b, int32_t *k_per_job);
 
 /* Release a batch.  NULL-safe. */
 void gj_batch_free(gj_batch *b);

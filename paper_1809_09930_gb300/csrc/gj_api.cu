@@ -141,6 +141,7 @@ IndexView view_of(const gj_index *h)
     v.u = h->u;
     v.e2 = h->e2;
     v.ew = h->ew;
+    v.ct = h->plain_ct;
     return v;
 }
 
@@ -197,7 +198,7 @@ int join_impl(gj_index *h, int part, int nparts, gj_pair *pairs_out, uint64_t ca
         h->last.total_ms = now_ms() - t_start;
         return GJ_OK;
     }
-    const int per_sm = h->tc_ready ? 1 : plain_ctas_per_sm(h->info.d);
+    const int per_sm = h->tc_ready ? 1 : plain_ctas_per_sm(h->info.d, h->plain_ct);
     if (per_sm < 1)
         return GJ_ERR_UNSUPPORTED;
     const int grid = h->sms * per_sm;
@@ -236,6 +237,7 @@ int join_impl(gj_index *h, int part, int nparts, gj_pair *pairs_out, uint64_t ca
     double kms = 0.0;
     uint32_t launches = 0;
     unsigned long long evaluated = 0, dims = 0, survivors = 0;
+    double busy_ms = 0.0;
 
     // ---- 1. sampled estimate of |R| (count-only over every S-th item), Sec. 3.2.2
     note_launch();
@@ -347,6 +349,7 @@ int join_impl(gj_index *h, int part, int nparts, gj_pair *pairs_out, uint64_t ca
         if (st != GJ_OK)
             break;
         ++launches;
+        busy_ms += (double)res.busy / (double)grid * 1e-6;
         evaluated += res.evaluated;
         dims += res.dims;
         survivors += res.survivors;
@@ -390,6 +393,7 @@ int join_impl(gj_index *h, int part, int nparts, gj_pair *pairs_out, uint64_t ca
     h->last.pairs = total;
     h->last.launches = launches;
     h->last.join_ms = kms;
+    h->last.busy_ms = busy_ms;
     h->last.total_ms = now_ms() - t_start;
     h->last.tc_survivors = survivors;
     h->last.evaluated = evaluated;
@@ -434,9 +438,18 @@ gj_index *gj_index_build_ex(const double *points, int64_t n, int32_t d, double e
         t_last_status = GJ_ERR_TOO_LARGE;
         return nullptr;
     }
-    if (cfg.k > std::min(d, MAXK)) {
+    if (cfg.k > std::min(d, MAXK) || cfg.query_block < 0 || (cfg.query_block > 0 && cfg.query_block < 8) ||
+        cfg.query_block > QB || (cfg.tile != 0 && cfg.tile != 32 && cfg.tile != 64)) {
         t_last_status = GJ_ERR_INVALID_ARG;
         return nullptr;
+    }
+    if ((cfg.flags & GJ_AUTOTUNE) && cfg.k == 0) {
+        // timed trials pick the settings; the winning trial's index is returned
+        gj_index *best = nullptr;
+        gj_tune_result r;
+        const int st = autotune_impl(points, n, d, eps, &cfg, &r, &best);
+        t_last_status = st;
+        return st == GJ_OK ? best : nullptr;
     }
     int dev = cfg.device;
     cudaError_t e;

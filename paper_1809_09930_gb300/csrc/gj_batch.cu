@@ -22,6 +22,8 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -52,7 +54,9 @@ struct gj_batch {
     cudaGraphExec_t graph;
     bool graph_ready;
     std::vector<uint64_t> n_job;
+    std::vector<int32_t> k_job;   // k of each job's grid
     uint64_t candidates;        // sum over jobs of the unordered candidate pairs of the grid
+    JoinCtl *ctl_host;          // pinned: the control block read back by the graph
 };
 
 namespace {
@@ -139,22 +143,20 @@ void gj_batch_free(gj_batch *b)
     cudaFree(b->jpos);
     cudaFreeHost(b->jpos_host);
     cudaFree(b->ctl);
+    cudaFreeHost(b->ctl_host);
     if (b->own_stream && b->stream)
         cudaStreamDestroy(b->stream);
     delete b;
 }
 
-gj_batch *gj_batch_build(const gj_job *jobs, int32_t njobs, const gj_config *cfg_in)
+}  // extern "C"
+
+namespace {
+
+// The combined structure of the jobs, job j's grid on ks[j] dimensions
+// (0 = the builder's own choice).
+gj_batch *build_batch(const gj_job *jobs, int32_t njobs, const gj_config &cfg, const int32_t *ks)
 {
-    gj_config cfg;
-    if (cfg_in)
-        cfg = *cfg_in;
-    else
-        gj_config_init(&cfg);
-    if (!jobs || njobs < 1) {
-        gj::set_last_status(GJ_ERR_INVALID_ARG);
-        return nullptr;
-    }
     int d_max = 1;
     int64_t n_total = 0;
     for (int32_t j = 0; j < njobs; ++j) {
@@ -210,13 +212,17 @@ gj_batch *gj_batch_build(const gj_job *jobs, int32_t njobs, const gj_config *cfg
     jc.stream = (void *)s;
     jc.device = dev;
     int64_t G_total = 0, A_total = 0, I_total = 0;
+    jc.flags &= ~(GJ_AUTOTUNE | GJ_TUNE_FORM);
+    jc.query_block = 0;
+    jc.tile = 0;
     for (int32_t j = 0; j < njobs && st == GJ_OK; ++j) {
-        jc.k = jobs[j].k;
+        jc.k = ks[j];
         hs[j] = gj_index_build_ex(jobs[j].points, jobs[j].n, jobs[j].d, jobs[j].eps, &jc);
         if (!hs[j]) {
             st = gj_last_status();
             break;
         }
+        b->k_job.push_back(hs[j]->info.k);
         G_total += hs[j]->G;
         I_total += hs[j]->nitems;
         b->candidates += hs[j]->info.candidate_pairs;
@@ -261,6 +267,7 @@ gj_batch *gj_batch_build(const gj_job *jobs, int32_t njobs, const gj_config *cfg
         if (e == cudaSuccess) e = cudaMalloc(&b->jpos, (size_t)njobs * sizeof(unsigned long long));
         if (e == cudaSuccess) e = cudaMallocHost(&b->jpos_host, (size_t)njobs * sizeof(unsigned long long));
         if (e == cudaSuccess) e = cudaMalloc(&b->ctl, sizeof(JoinCtl));
+        if (e == cudaSuccess) e = cudaMallocHost(&b->ctl_host, sizeof(JoinCtl));
         st = cuda_status(e);
     }
     int64_t P = 0, C = 0, A = 0, I = 0;
@@ -355,6 +362,174 @@ gj_batch *gj_batch_build(const gj_job *jobs, int32_t njobs, const gj_config *cfg
     return b;
 }
 
+JoinLaunch batch_launch(const gj_batch *b)
+{
+    JoinLaunch L{};
+    L.ix.X = b->X;
+    L.ix.orig = b->orig;
+    L.ix.cell_start = b->cell_start;
+    L.ix.adj_start = b->adj_start;
+    L.ix.adj = b->adj;
+    L.ix.items = b->items;
+    L.ix.n = b->n_total;
+    L.ix.npad = b->npad;
+    L.ix.d = b->d_max;
+    L.ix.u = -1;
+    L.queue = b->order;
+    L.qlimit = (uint32_t)b->nitems;
+    L.ctl = b->ctl;
+    L.out = nullptr;   // pairs go to the jobs' own buffers
+    return L;
+}
+
+// One count-only launch of the whole batch that also sums, per job, the SM
+// cycles its work items took (the autotuner's trial).
+int timed_trial(gj_batch *b, std::vector<unsigned long long> &cyc)
+{
+    cyc.assign((size_t)b->njobs, 0ull);
+    if (b->nitems == 0)
+        return GJ_OK;
+    cudaStream_t s = b->stream;
+    unsigned long long *dc = nullptr;
+    for (int32_t j = 0; j < b->njobs; ++j) {
+        b->jobs_host[j].out = nullptr;
+        b->jobs_host[j].cap = 0;
+    }
+    cudaError_t e = cudaMalloc(&dc, (size_t)b->njobs * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemsetAsync(dc, 0, (size_t)b->njobs * sizeof(unsigned long long), s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->jobs_dev, b->jobs_host, (size_t)b->njobs * sizeof(TcJob), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->jpos, 0, (size_t)b->njobs * sizeof(unsigned long long), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->ctl, 0, sizeof(JoinCtl), s);
+    if (e == cudaSuccess) e = tc_jobs_launch_attr(b->Kp);
+    if (e == cudaSuccess) {
+        note_launch();
+        e = launch_join_tc_jobs(batch_launch(b), b->XA, b->XB, b->Kp, b->jobs_dev, b->jpos, b->sms, s, dc);
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(cyc.data(), dc, (size_t)b->njobs * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->ctl_host, b->ctl, sizeof(JoinCtl), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(dc);
+    if (e != cudaSuccess)
+        return cuda_status(e);
+    if (b->ctl_host->err & kErrTimeout)
+        return GJ_ERR_TIMEOUT;
+    return b->ctl_host->err ? GJ_ERR_CUDA : GJ_OK;
+}
+
+// Picks of earlier tuned builds, per list of job shapes.
+std::mutex g_tune_mu;
+std::map<std::vector<uint64_t>, std::vector<int32_t>> g_tuned;
+
+std::vector<uint64_t> shape_key(const gj_job *jobs, int32_t njobs, const gj_config &cfg, int device)
+{
+    std::vector<uint64_t> key;
+    key.reserve((size_t)njobs * 3 + 2);
+    key.push_back((uint64_t)device);
+    key.push_back((uint64_t)(cfg.flags & (GJ_REORDER | GJ_SORTIDU | GJ_SHORTC)));
+    for (int32_t j = 0; j < njobs; ++j) {
+        uint64_t eb;
+        memcpy(&eb, &jobs[j].eps, sizeof(eb));
+        key.push_back((uint64_t)jobs[j].n);
+        key.push_back(((uint64_t)(uint32_t)jobs[j].d << 32) | (uint32_t)jobs[j].k);
+        key.push_back(eb);
+    }
+    return key;
+}
+
+}  // namespace
+
+extern "C" {
+
+gj_batch *gj_batch_build(const gj_job *jobs, int32_t njobs, const gj_config *cfg_in)
+{
+    gj_config cfg;
+    if (cfg_in)
+        cfg = *cfg_in;
+    else
+        gj_config_init(&cfg);
+    if (!jobs || njobs < 1) {
+        gj::set_last_status(GJ_ERR_INVALID_ARG);
+        return nullptr;
+    }
+    std::vector<int32_t> ks((size_t)njobs);
+    bool tune = false;
+    for (int32_t j = 0; j < njobs; ++j) {
+        ks[j] = jobs[j].k;
+        tune = tune || ((cfg.flags & GJ_AUTOTUNE) && jobs[j].k == 0 && jobs[j].d >= 1);
+    }
+    if (!tune)
+        return build_batch(jobs, njobs, cfg, ks.data());
+    int dev = cfg.device;
+    if (dev < 0)
+        cudaGetDevice(&dev);
+    const std::vector<uint64_t> key = shape_key(jobs, njobs, cfg, dev);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tuned.find(key);
+        if (it != g_tuned.end())
+            return build_batch(jobs, njobs, cfg, it->second.data());
+    }
+    // trials: every untuned job at k = 1, 2, 3 (capped at its d)
+    std::vector<std::vector<unsigned long long>> cyc;
+    std::vector<std::vector<int32_t>> used;
+    gj_batch *last = nullptr;
+    for (int kc = 1; kc <= 3; ++kc) {
+        std::vector<int32_t> kt(ks);
+        bool differs = kc == 1;
+        for (int32_t j = 0; j < njobs; ++j)
+            if (jobs[j].k == 0) {
+                kt[j] = std::min<int32_t>(kc, jobs[j].d);
+                differs = differs || kt[j] == kc;
+            }
+        if (!differs)
+            break;
+        gj_batch_free(last);
+        last = build_batch(jobs, njobs, cfg, kt.data());
+        if (!last)
+            return nullptr;
+        std::vector<unsigned long long> c;
+        const int st = timed_trial(last, c);
+        if (st != GJ_OK) {
+            gj_batch_free(last);
+            gj::set_last_status(st);
+            return nullptr;
+        }
+        cyc.push_back(c);
+        used.push_back(last->k_job);
+    }
+    std::vector<int32_t> pick(ks);
+    for (int32_t j = 0; j < njobs; ++j) {
+        if (jobs[j].k != 0)
+            continue;
+        size_t bt = 0;
+        for (size_t t = 1; t < cyc.size(); ++t)
+            if (cyc[t][j] < cyc[bt][j])
+                bt = t;
+        pick[j] = used[bt][j];
+    }
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tuned[key] = pick;
+    }
+    if (last && last->k_job == pick) {
+        gj::set_last_status(GJ_OK);
+        return last;
+    }
+    gj_batch_free(last);
+    return build_batch(jobs, njobs, cfg, pick.data());
+}
+
+int gj_batch_get_k(const gj_batch *b, int32_t *k_per_job)
+{
+    if (!b || !k_per_job)
+        return GJ_ERR_INVALID_ARG;
+    for (int32_t j = 0; j < b->njobs; ++j)
+        k_per_job[j] = b->k_job[(size_t)j];
+    return GJ_OK;
+}
+
 int gj_batch_self_join(gj_batch *b, gj_pair *const *outs, const uint64_t *caps, uint64_t *counts)
 {
     if (!b || !counts)
@@ -381,21 +556,7 @@ int gj_batch_self_join(gj_batch *b, gj_pair *const *outs, const uint64_t *caps, 
     cudaStream_t s = b->stream;
     cudaError_t e = cudaSuccess;
     if (!b->graph_ready) {
-        JoinLaunch L{};
-        L.ix.X = b->X;
-        L.ix.orig = b->orig;
-        L.ix.cell_start = b->cell_start;
-        L.ix.adj_start = b->adj_start;
-        L.ix.adj = b->adj;
-        L.ix.items = b->items;
-        L.ix.n = b->n_total;
-        L.ix.npad = b->npad;
-        L.ix.d = b->d_max;
-        L.ix.u = -1;
-        L.queue = b->order;
-        L.qlimit = (uint32_t)b->nitems;
-        L.ctl = b->ctl;
-        L.out = nullptr;   // pairs go to the jobs' own buffers
+        const JoinLaunch L = batch_launch(b);
         cudaGraph_t g = nullptr;
         e = tc_jobs_launch_attr(b->Kp);
         if (e == cudaSuccess)
@@ -408,6 +569,7 @@ int gj_batch_self_join(gj_batch *b, gj_pair *const *outs, const uint64_t *caps, 
                 launch_join_tc_jobs(L, b->XA, b->XB, b->Kp, b->jobs_dev, b->jpos, b->sms, s);
             cudaMemcpyAsync(b->jpos_host, b->jpos, (size_t)b->njobs * sizeof(unsigned long long),
                             cudaMemcpyDeviceToHost, s);
+            cudaMemcpyAsync(b->ctl_host, b->ctl, sizeof(JoinCtl), cudaMemcpyDeviceToHost, s);
             e = cudaStreamEndCapture(s, &g);
         }
         if (e == cudaSuccess)
@@ -427,6 +589,10 @@ int gj_batch_self_join(gj_batch *b, gj_pair *const *outs, const uint64_t *caps, 
         e = cudaStreamSynchronize(s);
     if (e != cudaSuccess)
         return cuda_status(e);
+    if (b->ctl_host->err & kErrTimeout)
+        return GJ_ERR_TIMEOUT;
+    if (b->ctl_host->err)
+        return GJ_ERR_CUDA;
     bool over = false;
     for (int32_t j = 0; j < b->njobs; ++j) {
         counts[j] = b->jpos_host[j];

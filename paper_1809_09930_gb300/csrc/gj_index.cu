@@ -717,6 +717,9 @@ int build_index(gj_index *h, const double *P, int64_t n, int d, double eps, int 
         }
         const bool tc = (flags & GJ_TC_FILTER) && ((d + 4 + 15) / 16) * 16 <= 128;
         h->qb = tc ? QB_TC : QB_PLAIN;
+        if (h->cfg.query_block > 0)
+            h->qb = std::min(h->cfg.query_block, tc ? QB_TC : QB);
+        h->plain_ct = tc ? 0 : h->cfg.tile;
         int kmax = std::min(d, MAXK);
         // the tensor-core filter wants large cells (full 128 x 128 tiles): index at most 3 dims
         k = (k_req > 0) ? std::min(k_req, kmax) : choose_k(d, nc_all, n, tc ? std::min(kmax, 3) : kmax);

@@ -48,6 +48,7 @@ struct JoinCtl {
     unsigned long long survivors;  // tensor-core filter survivors
     unsigned long long dims;       // dimensions evaluated (SHORTC depth summed over pairs)
     unsigned long long evaluated;  // candidate pairs evaluated
+    unsigned long long busy;       // ns from each CTA's start to its exit, summed over CTAs
     unsigned int head;             // main-queue dequeue counter (monotone across launches)
     unsigned int full;             // output filled during this launch
     unsigned int din_head;         // deferred-in dequeue counter
@@ -73,6 +74,7 @@ struct IndexView {
     int u;          // SORTIDU dimension (reordered index), -1 = off
     double e2;      // fl(eps*eps)
     double ew;      // SORTIDU window half-width (eps widened)
+    int ct;         // plain form: candidate tile (32 or 64), 0 = by d
 };
 
 struct JoinLaunch {
@@ -118,8 +120,8 @@ int build_index(gj_index *h, const double *P, int64_t n, int d, double eps, int 
 // ---- join kernels (gj_join.cu) -------------------------------------------
 cudaError_t launch_join_plain(const JoinLaunch &L, int grid, cudaStream_t s);
 cudaError_t launch_join_plain_direct(const JoinLaunch &L, int grid, cudaStream_t s);
-int plain_ctas_per_sm(int d);
-size_t plain_smem_bytes(int d);
+int plain_ctas_per_sm(int d, int ct = 0);
+size_t plain_smem_bytes(int d, int ct = 0);
 cudaError_t launch_fp64_probe(double *out, int iters, int grid, cudaStream_t s);
 
 // Per-job parameters of a many-jobs launch (gj_batch.cu).
@@ -138,10 +140,18 @@ size_t tc_staging_pairs_per_cta();
 int tc_threshold_bits(double eps, double sigma, double R0, int d, int Kp);
 cudaError_t tc_pack_into(const double *X, int64_t n, int64_t npad, int d, int Kp, double sigma, const double *centre,
                          int64_t row_off, void *XA, void *XB, cudaStream_t s);
+// job_cycles (nullable): per-job SM cycles between the epilogue's item ends,
+// summed over CTAs (the autotuner's per-job timing)
 cudaError_t launch_join_tc_jobs(const JoinLaunch &L, const void *XA, const void *XB, int Kp, const TcJob *jobs,
-                                unsigned long long *jpos, int grid, cudaStream_t s);
+                                unsigned long long *jpos, int grid, cudaStream_t s,
+                                unsigned long long *job_cycles = nullptr);
 cudaError_t tc_jobs_launch_attr(int Kp);
 void set_last_status(int st);
+
+// Autotuner (gj_tune.cu): runs the trials; *best_out (nullable) receives the
+// index of the pick, built, else it is freed.
+int autotune_impl(const double *points, int64_t n, int d, double eps, const gj_config *cfg, gj_tune_result *out,
+                  gj_index **best_out);
 
 }  // namespace gj
 
@@ -170,6 +180,7 @@ struct gj_index {
     double e2, ew;
     int sms;
     int qb;              // query block size the items were built with
+    int plain_ct;        // plain form: candidate tile, 0 = by d
     // tensor-core filter operands (GJ_TC_FILTER)
     bool tc_ready;
     void *XA, *XB;       // fp16 [npad + 512][Kp] in core-matrix order

@@ -27,6 +27,13 @@
 
 namespace gj {
 
+__device__ __forceinline__ unsigned long long globaltimer_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
 constexpr int JT = 256;               // threads per CTA
 constexpr unsigned FULL = 0xffffffffu;
 constexpr unsigned NONE = 0xffffffffu;
@@ -41,6 +48,7 @@ struct SmemHdr {
     uint32_t stop;            // abandon the current item (deferred)
     unsigned long long base;
     int ok;
+    long long t_start;        // clock at the CTA's start
     int64_t win_s[NBCHUNK];
     int64_t win_e[NBCHUNK];
     uint32_t win_b[NBCHUNK];
@@ -99,8 +107,10 @@ __global__ void __launch_bounds__(JT) k_join_plain(JoinLaunch L)
 
     unsigned long long my_count = 0, my_dims = 0, my_pairs = 0;
 
-    if (tid == 0)
+    if (tid == 0) {
         H.stg_cnt = 0;
+        H.t_start = (long long)globaltimer_ns();
+    }
 
     for (;;) {
         // ---- next item: deferred resume points first, then the main queue
@@ -368,6 +378,8 @@ __global__ void __launch_bounds__(JT) k_join_plain(JoinLaunch L)
         atomicAdd(&L.ctl->dims, my_dims);
         atomicAdd(&L.ctl->evaluated, my_pairs);
     }
+    if (tid == 0)
+        atomicAdd(&L.ctl->busy, (unsigned long long)((long long)globaltimer_ns() - H.t_start));
 }
 
 static size_t plain_smem(int d, int ct)
@@ -375,11 +387,11 @@ static size_t plain_smem(int d, int ct)
     return ((sizeof(SmemHdr) + 15) & ~size_t(15)) + (size_t)d * (QB + ct) * sizeof(double);
 }
 
-static int plain_ct(int d) { return d <= 32 ? 64 : 32; }
+static int plain_ct(int d, int ct = 0) { return ct == 32 || ct == 64 ? ct : (d <= 32 ? 64 : 32); }
 
-int plain_ctas_per_sm(int d)
+int plain_ctas_per_sm(int d, int ct_req)
 {
-    int ct = plain_ct(d);
+    int ct = plain_ct(d, ct_req);
     size_t sm = plain_smem(d, ct);
     int per = (int)((227 * 1024) / (sm + 1024));
     if (per > 4)
@@ -387,11 +399,11 @@ int plain_ctas_per_sm(int d)
     return per < 1 ? 0 : per;
 }
 
-size_t plain_smem_bytes(int d) { return plain_smem(d, plain_ct(d)); }
+size_t plain_smem_bytes(int d, int ct) { return plain_smem(d, plain_ct(d, ct)); }
 
 cudaError_t launch_join_plain_direct(const JoinLaunch &L, int grid, cudaStream_t s)
 {
-    const int ct = plain_ct(L.ix.d);
+    const int ct = plain_ct(L.ix.d, L.ix.ct);
     const size_t sm = plain_smem(L.ix.d, ct);
     cudaError_t e;
     if (ct == 64) {
@@ -412,7 +424,7 @@ cudaError_t launch_join_plain_direct(const JoinLaunch &L, int grid, cudaStream_t
 
 cudaError_t launch_join_plain(const JoinLaunch &L, int grid, cudaStream_t s)
 {
-    const int ct = plain_ct(L.ix.d);
+    const int ct = plain_ct(L.ix.d, L.ix.ct);
     const size_t sm = plain_smem(L.ix.d, ct);
     cudaError_t e;
     if (ct == 64) {

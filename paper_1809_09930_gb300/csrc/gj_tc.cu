@@ -85,12 +85,15 @@ struct TcShared {
     uint32_t sc[8][TC_SQ];
     unsigned long long surv;     // survivors (statistics)
     unsigned long long counted;  // pairs counted (count-only launches)
+    long long t_item;            // tuning launches: clock of the last item end
+    long long t_start;           // clock at the CTA's start
 };
 
 struct TcLaunch {
     JoinLaunch J;
     const TcJob *jobs;           // many-jobs launch: per-job parameters (else nullptr)
     unsigned long long *jpos;    // many-jobs launch: per-job pair counters
+    unsigned long long *job_cycles;   // many-jobs tuning launch: per-job SM cycles (else nullptr)
     const unsigned char *XA;
     const unsigned char *XB;
     int Kp;
@@ -328,6 +331,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
         S.cnt[0] = S.cnt[1] = 0;
         S.surv = 0;
         S.counted = 0;
+        S.t_start = (long long)globaltimer();
         fence_mbar_init();
     }
     if (warp == 1) {
@@ -572,6 +576,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
         unsigned long long slots = 0;
         uint32_t *const sq = S.sq[e], *const sc = S.sc[e];
         uint32_t nq = 0;
+        // tuning launches: the cycles from one item end to the next are the
+        // cost of the later item in the steady state (the epilogue is the
+        // pipeline's last stage); summed per job
+        if (etid == 0)
+            S.t_item = clock64();
         const float Tf0 = __int_as_float(T.Tbits);
         gj_pair *stg0 = count_only ? nullptr : L.staging + (size_t)blockIdx.x * 2 * TC_STG;
         // Cross-warp agreement only where a decision is needed: at the end of
@@ -712,6 +721,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
             }
             if (D.flags & F_TERM)
                 break;
+            if (T.job_cycles && item_end && etid == 0) {
+                const long long t_now = clock64();
+                atomicAdd(&T.job_cycles[L.ix.items[D.item].pad], (unsigned long long)(t_now - S.t_item));
+                S.t_item = t_now;
+            }
             if (count_only)
                 continue;
             if (!item_end && !flush)
@@ -779,6 +793,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
             atomicAdd(&L.ctl->survivors, S.surv);
         if (S.counted)
             atomicAdd(&L.ctl->counted, S.counted);
+        atomicAdd(&L.ctl->busy, (unsigned long long)((long long)globaltimer() - S.t_start));
     }
     if (S.abort) {
         // let copies and MMAs already issued land before the memory goes away
@@ -1012,12 +1027,13 @@ cudaError_t tc_jobs_launch_attr(int Kp)
 // (call tc_jobs_launch_attr first: this launcher sets no attribute, so it can
 // run inside a stream capture)
 cudaError_t launch_join_tc_jobs(const JoinLaunch &L, const void *XA, const void *XB, int Kp, const TcJob *jobs,
-                                unsigned long long *jpos, int grid, cudaStream_t s)
+                                unsigned long long *jpos, int grid, cudaStream_t s, unsigned long long *job_cycles)
 {
     TcLaunch T{};
     T.J = L;
     T.jobs = jobs;
     T.jpos = jpos;
+    T.job_cycles = jobs ? job_cycles : nullptr;
     T.XA = (const unsigned char *)XA;
     T.XB = (const unsigned char *)XB;
     T.Kp = Kp;

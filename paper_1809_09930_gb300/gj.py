@@ -32,6 +32,8 @@ GJ_REORDER = 1 << 0
 GJ_SORTIDU = 1 << 1
 GJ_SHORTC = 1 << 2
 GJ_TC_FILTER = 1 << 3
+GJ_AUTOTUNE = 1 << 4
+GJ_TUNE_FORM = 1 << 5
 GJ_DEFAULT_FLAGS = GJ_REORDER | GJ_SORTIDU | GJ_SHORTC
 
 
@@ -43,7 +45,14 @@ class GJError(RuntimeError):
 
 class gj_config(C.Structure):
     _fields_ = [("k", C.c_int32), ("flags", C.c_uint32), ("stream", C.c_void_p),
-                ("batch_pairs", C.c_uint64), ("device", C.c_int32), ("reserved", C.c_uint32 * 7)]
+                ("batch_pairs", C.c_uint64), ("device", C.c_int32), ("query_block", C.c_int32),
+                ("tile", C.c_int32), ("reserved", C.c_uint32 * 5)]
+
+
+class gj_tune_result(C.Structure):
+    _fields_ = [("k", C.c_int32), ("flags", C.c_uint32), ("query_block", C.c_int32), ("tile", C.c_int32),
+                ("batch_pairs", C.c_uint64), ("est_pairs", C.c_uint64), ("build_ms", C.c_double),
+                ("join_ms", C.c_double), ("trials", C.c_int32), ("reserved", C.c_int32)]
 
 
 class gj_job(C.Structure):
@@ -63,14 +72,14 @@ class gj_join_stats(C.Structure):
     _fields_ = [("pairs", C.c_uint64), ("launches", C.c_uint32), ("batches_planned", C.c_uint32),
                 ("batch_pairs", C.c_uint64), ("estimate", C.c_uint64), ("tc_survivors", C.c_uint64),
                 ("evaluated", C.c_uint64), ("dims", C.c_uint64), ("join_ms", C.c_double),
-                ("estimate_ms", C.c_double), ("total_ms", C.c_double)]
+                ("estimate_ms", C.c_double), ("total_ms", C.c_double), ("busy_ms", C.c_double)]
 
 
 EXPORTS = ["gj_config_init", "gj_index_build", "gj_index_build_ex", "gj_self_join",
            "gj_self_join_part", "gj_index_get_info", "gj_last_join_stats", "gj_free",
            "gj_last_status", "gj_status_string", "gj_version", "gj_probe_fp64_tflops",
            "gj_kernel_launches", "gj_debug_tc_tile", "gj_self_join_noalloc", "gj_batch_build",
-           "gj_batch_self_join", "gj_batch_get_info", "gj_batch_free"]
+           "gj_batch_self_join", "gj_batch_get_info", "gj_batch_free", "gj_autotune", "gj_batch_get_k"]
 
 _lib = None
 
@@ -123,6 +132,11 @@ def load(path: str | None = None):
     lib.gj_batch_free.restype = None
     lib.gj_batch_free.argtypes = [V]
     lib.gj_self_join_noalloc.argtypes = [V, C.c_int32, C.c_int32, V, C.c_uint64, C.POINTER(C.c_uint64)]
+    lib.gj_autotune.restype = C.c_int
+    lib.gj_autotune.argtypes = [V, C.c_int64, C.c_int32, C.c_double, C.POINTER(gj_config),
+                                C.POINTER(gj_tune_result)]
+    lib.gj_batch_get_k.restype = C.c_int
+    lib.gj_batch_get_k.argtypes = [V, C.POINTER(C.c_int32)]
     if path is None:
         _lib = lib
     return lib
@@ -194,6 +208,18 @@ def gj_index_build_ex(points, eps: float, cfg: gj_config) -> int:
     if not h:
         raise GJError(gj_last_status(), "gj_index_build_ex")
     return h
+
+
+def gj_autotune(points, eps: float, cfg: gj_config | None = None) -> dict:
+    """The autotuner's pick for these points (timed trials on the device)."""
+    p, n, d, keep = _ptr_points(points)
+    cfg = cfg if cfg is not None else gj_config_init()
+    r = gj_tune_result()
+    st = load().gj_autotune(p, n, d, float(eps), C.byref(cfg), C.byref(r))
+    del keep
+    if st != GJ_OK:
+        raise GJError(st, "gj_autotune")
+    return {f: getattr(r, f) for f, _ in gj_tune_result._fields_ if f != "reserved"}
 
 
 def gj_self_join(h: int, out=None) -> tuple[int, int]:
@@ -326,6 +352,14 @@ def gj_batch_get_info(b: int) -> dict:
     return {"work_items": wi.value, "total_points": tp.value, "candidate_pairs": cp.value}
 
 
+def gj_batch_get_k(b: int, njobs: int) -> list[int]:
+    ks = (C.c_int32 * njobs)()
+    st = load().gj_batch_get_k(b, ks)
+    if st != GJ_OK:
+        raise GJError(st, "gj_batch_get_k")
+    return [int(k) for k in ks]
+
+
 def gj_batch_free(b: int) -> None:
     if b:
         load().gj_batch_free(b)
@@ -339,13 +373,16 @@ class Index:
     """Owns a gj_index handle."""
 
     def __init__(self, points, eps: float, k: int = 0, flags: int = GJ_DEFAULT_FLAGS,
-                 stream=None, batch_pairs: int = 0, device: int = -1):
+                 stream=None, batch_pairs: int = 0, device: int = -1, query_block: int = 0,
+                 tile: int = 0):
         cfg = gj_config_init()
         cfg.k = int(k)
         cfg.flags = int(flags)
         cfg.stream = int(stream) if stream else None
         cfg.batch_pairs = int(batch_pairs)
         cfg.device = int(device)
+        cfg.query_block = int(query_block)
+        cfg.tile = int(tile)
         self.h = gj_index_build_ex(points, eps, cfg)
 
     def close(self):

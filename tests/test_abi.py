@@ -66,3 +66,25 @@ def test_no_gpu_build_fails_loudly(lib):
     with pytest.raises(gj.GJError) as e:
         gj.Index(np.zeros((4, 2)), 0.5)
     assert e.value.status == gj.GJ_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("field,value", [("query_block", 7), ("query_block", 129), ("query_block", -1),
+                                         ("tile", 48), ("tile", 16), ("k", 9)])
+def test_config_ranges_rejected_before_any_device_call(lib, field, value):
+    """Out-of-range settings fail with GJ_ERR_INVALID_ARG (checked on the host,
+    before the device is touched, so this runs without a GPU)."""
+    import numpy as np
+    from paper_1809_09930_gb300 import gj
+    cfg = gj.gj_config_init()
+    setattr(cfg, field, value)
+    with pytest.raises(gj.GJError) as e:
+        gj.gj_index_build_ex(np.zeros((16, 8)), 0.5, cfg)
+    assert e.value.status == gj.GJ_ERR_INVALID_ARG
+
+
+def test_config_layout_matches_header(lib):
+    """gj_config keeps its size: the new fields took reserved words."""
+    import ctypes
+    from paper_1809_09930_gb300 import gj
+    assert ctypes.sizeof(gj.gj_config) == 4 + 4 + 8 + 8 + 4 + 4 + 4 + 5 * 4   # 56, as before
+    assert ctypes.sizeof(gj.gj_tune_result) == 4 * 4 + 8 * 4 + 4 * 2
