@@ -124,6 +124,32 @@ class ClockSampler:
 
 # ---------------------------------------------------------------------------
 
+def rank_max(dist, x: float, device: str = "cuda") -> float:
+    """The maximum of x over the ranks (the step time: the slowest rank)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def rank_sum(dist, xs: list, device: str = "cuda") -> list:
+    """Element-wise sums over the ranks (per-rank pair counts of the entity
+    partition add up to |R|: the parts are disjoint)."""
+    if dist is None:
+        return list(xs)
+    import torch
+    t = torch.tensor([int(v) for v in xs], dtype=torch.int64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return [int(v) for v in t.tolist()]
+
+
+def workload_name(args, runs) -> str:
+    return (f"paper-scale uniform [0,1)^d, n={args.n}, d in {[r['d'] for r in runs]}, "
+            f"eps for 32 mean neighbours")
+
+
 def workload(args):
     with open(WORKLOADS) as f:
         W = json.load(f)
@@ -168,16 +194,21 @@ def reference_arm(args, runs):
     import oracle
     oracle.build()
     cb = None
-    vals = []
+    vals, walls = [], []
+    # each step a bounded sample, sized so that the whole run stays near 2.5 minutes
+    budget = max(3.0, min(20.0, 150.0 / max(1, args.warmup + steps)))
     for _ in range(args.warmup + steps):
-        cb = cpu_baseline(runs, budget_s=20.0)
+        t0 = time.perf_counter()
+        cb = cpu_baseline(runs, budget_s=budget)
+        walls.append(time.perf_counter() - t0)
         vals.append(cb["value"])
     v = statistics.median(vals[args.warmup:]) if steps else vals[-1]
+    ms_step = 1e3 * statistics.median(walls[args.warmup:] if steps else walls)
     out = {"metric": "distance evals/s (self-join, exact pair set)", "value": v,
            "unit": "distance evals/s", "n_gpus": args.gpus, "steps": steps, "warmup": args.warmup,
-           "ms_per_step": None, "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
+           "ms_per_step": ms_step, "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
            "dtype": "f64", "data": "synthetic", "impl": "reference",
-           "config": {"workload": f"paper-scale uniform, n={args.n}, d in {[r['d'] for r in runs]}",
+           "config": {"workload": workload_name(args, runs),
                       "form": "cpu-oracle", "sample": cb["sample"]},
            "cpu_baseline": dict(cb, value=v),
            "e2e": {"value": v, "unit": "distance evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -451,11 +482,9 @@ def main():
         dist.barrier()
     launches = gj.gj_kernel_launches() - l0
     clk = clocks.stop()
-    ms = ev0.elapsed_time(ev1)
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = rank_max(dist, ev0.elapsed_time(ev1))
+    ds = sorted(col["pairs"])
+    col["pairs"] = dict(zip(ds, rank_sum(dist, [col["pairs"][d] for d in ds])))
     # evals: the whole job's candidate pairs (parts of one join sum to the join)
     value = evals / (ms * 1e-3)
 
@@ -509,10 +538,7 @@ def main():
             ev += e2e_step()
         torch.cuda.synchronize()
         e2e_s = time.perf_counter() - t0
-        if dist:
-            t = torch.tensor([e2e_s], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
+        e2e_s = rank_max(dist, e2e_s)
         h2d = sum(X.nbytes for _, X, _ in data)
         d2h = sum(8 * col["pairs"][r["d"]] for r, _, _ in data)
         e2e = {"value": ev / e2e_s, "unit": "distance evals/s", "h2d_bytes_per_step": h2d,
@@ -545,8 +571,7 @@ def main():
         "vs_baseline": None,
         "dtype": "f64" if args.form == "plain" else "f16xf16->f32 filter + f64 recheck",
         "data": "synthetic",
-        "config": {"workload": f"paper-scale uniform [0,1)^d, n={args.n}, d in {[r['d'] for r in runs]}, "
-                               f"eps for 32 mean neighbours",
+        "config": {"workload": workload_name(args, runs),
                    "form": args.form, "eps": {r["d"]: r["eps"] for r in runs}, "k": col["k"],
                    "pairs": col["pairs"], "parallelism": f"entity partition x{world}",
                    "l2": "inputs larger than L2 (>=256 MB per point set)",

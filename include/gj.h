@@ -158,8 +158,9 @@ typedef struct {
  * block and the plain form's candidate tile by timed trials: for each
  * candidate setting it builds the index and times a count-only join over a
  * fixed, load-stratified share of the work items (one part of an entity
- * partition, Sec. 6.2), extrapolated to the whole queue; the setting with the
- * least build + join time wins.  k runs over 1..min(d, 8) (1..3 for the
+ * partition, Sec. 6.2; the part sized so that a trial's join takes about
+ * 40 ms), extrapolated to the whole queue; the setting with the least build +
+ * join time wins (by at least 2 %, else the earlier setting stays).  k runs over 1..min(d, 8) (1..3 for the
  * tensor-core form), the plain tiles over query blocks {120, 64} x candidate
  * tiles {64, 32}.  With GJ_TUNE_FORM in cfg->flags both forms are tried,
  * else only the form cfg->flags names.  The result batch size b_s is then
@@ -199,6 +200,22 @@ int gj_self_join(gj_index *h, gj_pair *pairs_out, uint64_t cap, uint64_t *count)
  */
 int gj_self_join_part(gj_index *h, int32_t part, int32_t nparts, gj_pair *pairs_out,
                       uint64_t cap, uint64_t *count);
+
+/*
+ * The neighbour table (Alg. 1, constructNeighborTable; Sec. 3.2.2: the
+ * result's key/value pairs stored with each key once).  Compressed sparse
+ * rows over the original point order: the neighbours of point a are
+ * nbr[row_start[a] .. row_start[a+1]), ascending, a itself included.  Built on
+ * the device from a join into library-allocated device memory (8 bytes per
+ * pair, plus 20 bytes per pair while the pairs are sorted).
+ *   row_start  device memory of the handle's device, int64 [n + 1]
+ *   nbr        device memory, uint32 [cap]
+ *   count      out: |R|
+ * Returns GJ_OK; GJ_ERR_CAPACITY when |R| > cap (*count = |R|, nothing
+ * written); GJ_ERR_INVALID_ARG when a buffer is not device memory; or another
+ * error code.
+ */
+int gj_neighbor_table(gj_index *h, int64_t *row_start, uint32_t *nbr, uint64_t cap, uint64_t *count);
 
 /*
  * A self-join that allocates nothing (no paper counterpart).  gj_self_join

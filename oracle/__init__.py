@@ -15,6 +15,7 @@ Functions (paper section each follows):
   index_loss(n, k)                  l(n,k) of Sec. 4.1
   selectivity(R, n)                 S_D of Sec. 5.2
   depth_stats(X, eps, perm, qs)     SHORTC depth per candidate pair (Sec. 4.4)
+  neighbor_table(pairs, n)          constructNeighborTable of Alg. 1 (Sec. 3.2.2) as CSR
 Pairs are returned as an (m, 2) uint32 array sorted by (a, b).
 """
 from __future__ import annotations
@@ -249,3 +250,17 @@ def depth_stats(X, eps: float, perm, queries, nthreads: int | None = None) -> tu
     _load().gjo_depth_stats(X.ctypes.data, n, d, float(eps), perm.ctypes.data, qs.ctypes.data,
                             qs.size, _threads(nthreads), C.byref(ds), C.byref(pc))
     return int(ds.value), int(pc.value)
+
+
+def neighbor_table(pairs, n: int) -> tuple[np.ndarray, np.ndarray]:
+    """constructNeighborTable (Alg. 1; Sec. 3.2.2): the key/value result pairs
+    stored with each key once.  As compressed sparse rows over the point order:
+    the neighbours of a are nbr[row_start[a]:row_start[a+1]], ascending.
+    A plain group-by: sort the pairs by (key, value), count the keys."""
+    p = np.asarray(pairs, dtype=np.int64).reshape(-1, 2)
+    order = np.lexsort((p[:, 1], p[:, 0]))
+    nbr = p[order, 1].astype(np.uint32)
+    counts = np.bincount(p[:, 0], minlength=n) if p.size else np.zeros(n, dtype=np.int64)
+    row_start = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(counts, out=row_start[1:])
+    return row_start, nbr

@@ -58,12 +58,17 @@ constexpr uint32_t TC_STG = 1u << 18;   // staging pairs per half per CTA (4 til
 constexpr uint64_t TC_LIMIT_NS = 4000000000ull;   // 4 s per wait
 constexpr int TC_SQ = 64;        // survivor queue per epilogue warp
 
-enum : uint32_t { F_FIRST = 1, F_LAST = 2, F_MARKER = 4, F_TRUNC = 8, F_TERM = 16, F_SELF = 32, F_FLUSH = 64 };
+enum : uint32_t { F_FIRST = 1, F_LAST = 2, F_MARKER = 4, F_TRUNC = 8, F_TERM = 16, F_FLUSH = 64 };
 
+// One candidate tile: rows r0 .. r0+255 of the B operand, of which the rows
+// in the searched windows are valid (bit c of mask = row r0 + c).  Windows of
+// several adjacent cells share a tile when they lie within 256 rows of each
+// other (the adjacent cells of a query cell come in ascending position order).
 struct TileDesc {
     uint32_t item, tile, flags, pad;
     uint32_t qbeg, qlen, qa, r0;
-    uint32_t ws, we, p2, p3;
+    uint32_t p2, p3, pad2, pad3;
+    uint32_t mask[8];
 };
 
 struct TcShared {
@@ -87,6 +92,7 @@ struct TcShared {
     unsigned long long counted;  // pairs counted (count-only launches)
     long long t_item;            // tuning launches: clock of the last item end
     long long t_start;           // clock at the CTA's start
+    uint32_t cmask[8];           // producer: valid rows of the tile being packed
 };
 
 struct TcLaunch {
@@ -102,6 +108,16 @@ struct TcLaunch {
     uint32_t a_bytes, b_bytes;
     uint32_t off_b, off_s;
 };
+
+// Set bits [lo, hi) of a 256-bit row mask (0 <= lo < hi <= 256).
+__device__ __forceinline__ void tc_set_rows(uint32_t *m, uint32_t lo, uint32_t hi)
+{
+    for (uint32_t w = lo >> 5; w <= ((hi - 1u) >> 5); ++w) {
+        const uint32_t a = max(lo, w * 32u) - w * 32u, b = min(hi, w * 32u + 32u) - w * 32u;
+        const uint32_t top = b >= 32u ? 0xffffffffu : ((1u << b) - 1u);
+        m[w] |= top & ~((1u << a) - 1u);
+    }
+}
 
 __device__ __forceinline__ int64_t tc_lower_u(const double *__restrict__ U, int64_t lo, int64_t hi, double ref,
                                               double ew)
@@ -260,7 +276,7 @@ __device__ __forceinline__ uint32_t hit_mask32(const uint32_t (&v)[32], float Tf
 // the queue through the FP64 recheck when it would overflow.  Returns the new
 // queue length.
 __device__ __noinline__ uint32_t tc_queue_bits(const TcLaunch *__restrict__ T, uint32_t mask, uint32_t col0,
-                                               uint32_t qpos, uint32_t r0, uint32_t ws, uint32_t we, bool self,
+                                               uint32_t qpos, uint32_t r0,
                                                uint32_t *sq, uint32_t *sc, uint32_t nq, gj_pair *stg, uint32_t *cnt,
                                                uint32_t *flush_req, unsigned long long *surv_sh,
                                                unsigned long long *counted_sh, uint32_t job)
@@ -274,7 +290,9 @@ __device__ __noinline__ uint32_t tc_queue_bits(const TcLaunch *__restrict__ T, u
             break;
         const uint32_t cpos = r0 + col0 + (have ? (uint32_t)(__ffs(mask) - 1) : 0u);
         mask &= mask - 1u;
-        const bool h = have && cpos >= ws && cpos < we && (!self || cpos >= qpos);
+        // the mask holds valid rows only; j >= i keeps one orientation (rows of
+        // the other searched cells all lie after the query cell)
+        const bool h = have && cpos >= qpos;
         const unsigned bal = __ballot_sync(0xffffffffu, h);
         if (!bal)
             continue;
@@ -412,11 +430,44 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
             uint32_t tile_idx = 0;
             bool have = false, first = true, trunc = false;
             TileDesc pend{};
+            // the tile being packed: rows [cr0, cr0 + TC_N); its valid-row mask
+            // lives in shared memory (lane 0); every other value is warp-uniform
+            bool open = false;
+            uint32_t cr0 = 0;
+            auto close_tile = [&]() {
+                if (!open)
+                    return;
+                open = false;
+                if (tile_idx >= resume) {
+                    if (lane == 0) {
+                        // another CTA filled the output: stop (polled every 32 tiles;
+                        // tiles made meanwhile are discarded by the failed commit)
+                        if (!count_only && (tile_idx & 31u) == 0 && *(volatile unsigned int *)&L.ctl->full) {
+                            trunc = true;
+                        } else {
+                            if (have) {
+                                if (first)
+                                    pend.flags |= F_FIRST;
+                                first = false;
+                                if (!push(pend, true))
+                                    dead = true;
+                            }
+                            pend = TileDesc{item, tile_idx, 0u, 0u, it.qbeg, it.qlen, qa, cr0, job, jtb, 0u, 0u};
+#pragma unroll
+                            for (int w = 0; w < 8; ++w)
+                                pend.mask[w] = S.cmask[w];
+                            have = true;
+                        }
+                    }
+                    trunc = __shfl_sync(0xffffffffu, trunc, 0);
+                    dead = __shfl_sync(0xffffffffu, dead, 0);
+                }
+                ++tile_idx;
+            };
             for (int64_t nb0 = nb_begin; nb0 < nb_end && !trunc && !dead; nb0 += 32) {
                 int64_t ws = 0, we = 0;
-                uint32_t b = 0;
                 if (nb0 + lane < nb_end) {
-                    b = L.ix.adj[nb0 + lane];
+                    const uint32_t b = L.ix.adj[nb0 + lane];
                     if (b == it.cell) {
                         ws = it.qbeg;
                         we = cell_end;
@@ -432,41 +483,35 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
                 }
                 const int nw = (int)min((int64_t)32, nb_end - nb0);
                 for (int w = 0; w < nw && !trunc && !dead; ++w) {
-                    const int64_t s0 = __shfl_sync(0xffffffffu, ws, w);
+                    int64_t s0 = __shfl_sync(0xffffffffu, ws, w);
                     const int64_t e0 = __shfl_sync(0xffffffffu, we, w);
-                    const uint32_t bw = __shfl_sync(0xffffffffu, b, w);
-                    if (s0 >= e0)
-                        continue;
-                    for (int64_t r0 = s0 & ~(int64_t)7; r0 < e0; r0 += TC_N, ++tile_idx) {
-                        if (tile_idx < resume)
-                            continue;
-                        if (lane == 0) {
-                            // another CTA filled the output: stop (polled every 32 tiles;
-                            // tiles made meanwhile are discarded by the failed commit)
-                            if (!count_only && (tile_idx & 31u) == 0 &&
-                                *(volatile unsigned int *)&L.ctl->full) {
-                                trunc = true;
-                            } else {
-                                if (have) {
-                                    if (first)
-                                        pend.flags |= F_FIRST;
-                                    first = false;
-                                    if (!push(pend, true))
-                                        dead = true;
-                                }
-                                pend = TileDesc{item, tile_idx, (bw == it.cell) ? F_SELF : 0u, 0u,
-                                                it.qbeg, it.qlen, qa, (uint32_t)r0,
-                                                (uint32_t)s0, (uint32_t)e0, job, jtb};
-                                have = true;
-                            }
-                        }
-                        trunc = __shfl_sync(0xffffffffu, trunc, 0);
-                        dead = __shfl_sync(0xffffffffu, dead, 0);
+                    while (s0 < e0 && !trunc && !dead) {
+                        // (windows come in ascending order; one that does not
+                        // starts a tile of its own)
+                        if (open && (s0 >= (int64_t)cr0 + TC_N || s0 < (int64_t)cr0))
+                            close_tile();
                         if (trunc || dead)
                             break;
+                        if (!open) {
+                            open = true;
+                            cr0 = (uint32_t)(s0 & ~(int64_t)7);
+                            if (lane == 0) {
+#pragma unroll
+                                for (int k2 = 0; k2 < 8; ++k2)
+                                    S.cmask[k2] = 0u;
+                            }
+                        }
+                        const int64_t hi = min(e0, (int64_t)cr0 + TC_N);
+                        if (lane == 0)
+                            tc_set_rows(S.cmask, (uint32_t)(s0 - cr0), (uint32_t)(hi - cr0));
+                        s0 = hi;
+                        if (s0 < e0)
+                            close_tile();   // the window runs on past this tile
                     }
                 }
             }
+            if (!trunc && !dead)
+                close_tile();
             if (lane == 0 && !dead) {
                 if (have && !trunc) {
                     pend.flags |= F_LAST | (first ? F_FIRST : 0u);
@@ -475,7 +520,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
                 } else {
                     TileDesc M{item, first ? resume : 0u, F_MARKER | F_LAST | (first ? F_FIRST : 0u) |
                                                          (trunc ? F_TRUNC : 0u),
-                               0u, it.qbeg, it.qlen, qa, 0u, 0u, 0u, job, jtb};
+                               0u, it.qbeg, it.qlen, qa, 0u, job, jtb, 0u, 0u};
                     if (!push(M, false))
                         dead = true;
                 }
@@ -620,6 +665,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
             bool anyhit = false;
             uint32_t qpos = 0;
             if (is_tile && !failed) {
+                // valid rows of this thread's 128 columns, read before the
+                // accumulator (and with it the descriptor slot) is released
+                const uint32_t *vmp = S.tdesc[acc].mask + hh * 4;
+                const uint32_t vm0 = vmp[0], vm1 = vmp[1], vm2 = vmp[2], vm3 = vmp[3];
                 const uint32_t row = (uint32_t)(q * 32 + lane);
                 qpos = D.qa + row;
                 const bool rvalid = qpos >= D.qbeg && qpos < D.qbeg + D.qlen;
@@ -634,9 +683,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
                     if (__any_sync(0xffffffffu, ha || hb)) {
                         anyhit = true;
                         if (ha)
-                            hm0 = hit_mask32(va, Tf);
+                            hm0 = hit_mask32(va, Tf) & vm0;
                         if (hb)
-                            hm1 = hit_mask32(vb, Tf);
+                            hm1 = hit_mask32(vb, Tf) & vm1;
                     }
                 }
                 {
@@ -649,14 +698,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
                     if (__any_sync(0xffffffffu, ha || hb)) {
                         anyhit = true;
                         if (ha)
-                            hm2 = hit_mask32(va, Tf);
+                            hm2 = hit_mask32(va, Tf) & vm2;
                         if (hb)
-                            hm3 = hit_mask32(vb, Tf);
+                            hm3 = hit_mask32(vb, Tf) & vm3;
                     }
                 }
                 if (etid == 0) {
-                    const uint32_t lo = max(D.r0, D.ws), hi = min(D.r0 + (uint32_t)TC_N, D.we);
-                    slots += (unsigned long long)D.qlen * (hi > lo ? hi - lo : 0u);
+                    const uint32_t *m = S.tdesc[acc].mask;
+                    const uint32_t nv = __popc(m[0]) + __popc(m[1]) + __popc(m[2]) + __popc(m[3]) + __popc(m[4]) +
+                                        __popc(m[5]) + __popc(m[6]) + __popc(m[7]);
+                    slots += (unsigned long long)D.qlen * nv;
                 }
             }
             // A warp with few hits queues them after releasing the accumulator.
@@ -675,19 +726,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
                     mbar_arrive(&S.tmem_empty[acc]);
             }
             if (anyhit) {
-                const bool self = (D.flags & F_SELF) != 0;
                 const uint32_t cb = (uint32_t)hh * 128u;
                 if (__any_sync(0xffffffffu, hm0 != 0u))
-                    nq = tc_queue_bits(&T, hm0, cb + 0u, qpos, D.r0, D.ws, D.we, self, sq, sc, nq, stg, &S.cnt[half],
+                    nq = tc_queue_bits(&T, hm0, cb + 0u, qpos, D.r0, sq, sc, nq, stg, &S.cnt[half],
                                        &S.flush_req, &S.surv, &S.counted, D.p2);
                 if (__any_sync(0xffffffffu, hm1 != 0u))
-                    nq = tc_queue_bits(&T, hm1, cb + 32u, qpos, D.r0, D.ws, D.we, self, sq, sc, nq, stg, &S.cnt[half],
+                    nq = tc_queue_bits(&T, hm1, cb + 32u, qpos, D.r0, sq, sc, nq, stg, &S.cnt[half],
                                        &S.flush_req, &S.surv, &S.counted, D.p2);
                 if (__any_sync(0xffffffffu, hm2 != 0u))
-                    nq = tc_queue_bits(&T, hm2, cb + 64u, qpos, D.r0, D.ws, D.we, self, sq, sc, nq, stg, &S.cnt[half],
+                    nq = tc_queue_bits(&T, hm2, cb + 64u, qpos, D.r0, sq, sc, nq, stg, &S.cnt[half],
                                        &S.flush_req, &S.surv, &S.counted, D.p2);
                 if (__any_sync(0xffffffffu, hm3 != 0u))
-                    nq = tc_queue_bits(&T, hm3, cb + 96u, qpos, D.r0, D.ws, D.we, self, sq, sc, nq, stg, &S.cnt[half],
+                    nq = tc_queue_bits(&T, hm3, cb + 96u, qpos, D.r0, sq, sc, nq, stg, &S.cnt[half],
                                        &S.flush_req, &S.surv, &S.counted, D.p2);
                 if (early && nq) {
                     unsigned long long c = 0;

@@ -10,11 +10,14 @@
 //     r mod N_b, so a part is a load-stratified sample).  The part's join time
 //     is the kernel's busy time -- each CTA's start-to-exit time averaged over
 //     the grid, i.e. the part's work spread evenly, without the tail a small
-//     sample has -- scaled by N_b;
+//     sample has -- scaled by N_b.  N_b comes from a first, finely sampled
+//     trial of the builder's own choice, so that a trial's join takes about
+//     40 ms (at most 32 parts);
 //   * k sweeps 1..min(d, 8) (1..3 for the tensor-core form) with the default
 //     tiles and stops once the cost has grown past twice the best for two
 //     consecutive k; then the tiles are tried at the best k;
-//   * the least build + join time wins; its index is kept when the caller
+//   * the least build + join time wins (a later setting must be 2 % faster,
+//     so near-ties keep the smaller k and the default tiles); its index is kept when the caller
 //     wants it (gj_index_build_ex with GJ_AUTOTUNE);
 //   * b_s comes from the winner's |R| estimate, a timed device-to-host copy
 //     and the measured per-launch overhead (see pick_batch_pairs).
@@ -44,18 +47,22 @@ struct Trial {
     double cost() const { return build_ms + join_ms; }
 };
 
-// Parts of the trial's entity partition: at least two work items per
-// resident CTA in the timed part, at most 32 parts.
-int trial_parts(const gj_index *h)
+constexpr double kTrialTargetMs = 40.0;   // sampled join time a trial aims for
+constexpr int kMaxParts = 32;
+
+// Parts of the trial's entity partition: np_req when given, else as many as
+// leave at least two work items per resident CTA in the timed part (at most
+// kMaxParts); never so many that the part has fewer items than CTAs.
+int trial_parts(const gj_index *h, int np_req)
 {
     const int per_sm = h->tc_ready ? 1 : std::max(1, plain_ctas_per_sm(h->info.d, h->plain_ct));
     const int64_t ctas = (int64_t)h->sms * per_sm;
-    const int64_t np = h->nitems / (2 * ctas);
-    return (int)std::max<int64_t>(1, std::min<int64_t>(32, np));
+    const int64_t cap = std::max<int64_t>(1, std::min<int64_t>(kMaxParts, h->nitems / (2 * ctas)));
+    return (int)(np_req > 0 ? std::min<int64_t>(np_req, cap) : cap);
 }
 
 // One timed trial.  On success *h_out holds the trial's index.
-int run_trial(const double *P, int64_t n, int d, double eps, Trial *t, gj_index **h_out)
+int run_trial(const double *P, int64_t n, int d, double eps, int np_req, Trial *t, gj_index **h_out)
 {
     *h_out = nullptr;
     gj_config c = t->cfg;
@@ -70,7 +77,7 @@ int run_trial(const double *P, int64_t n, int d, double eps, Trial *t, gj_index 
         return e == cudaErrorMemoryAllocation ? GJ_ERR_OOM : GJ_ERR_CUDA;
     }
     t->build_ms = wall_ms() - t0;
-    const int np = trial_parts(h);
+    const int np = trial_parts(h, np_req);
     const int part = np / 2;
     uint64_t cnt = 0;
     double best = INFINITY;
@@ -216,13 +223,31 @@ int autotune_impl(const double *points, int64_t n, int d, double eps, const gj_c
     bool have = false;
     gj_index *best_h = nullptr;
     int trials = 0, st = GJ_OK;
+    // calibration: the builder's own choice, sampled finely, sizes the sample
+    // of every trial so that its join takes about kTrialTargetMs
+    int np_req = kMaxParts;
+    {
+        Trial t;
+        t.cfg = base;
+        t.cfg.flags &= ~GJ_TUNE_FORM;
+        if (!forms[0])
+            t.cfg.flags &= ~GJ_TC_FILTER;
+        t.cfg.k = 0;
+        gj_index *h = nullptr;
+        st = run_trial(P, n, d, eps, kMaxParts, &t, &h);
+        ++trials;
+        gj_free(h);
+        if (st == GJ_OK)
+            np_req = (int)std::max(1.0, std::min((double)kMaxParts, floor(t.join_ms / kTrialTargetMs)));
+    }
     auto consider = [&](Trial &t) -> int {
         gj_index *h = nullptr;
-        const int s2 = run_trial(P, n, d, eps, &t, &h);
+        const int s2 = run_trial(P, n, d, eps, np_req, &t, &h);
         ++trials;
         if (s2 != GJ_OK)
             return s2;
-        if (!have || t.cost() < best.cost()) {
+        // a later setting must win by 2 %: ties go to the earlier (smaller k, default tiles)
+        if (!have || t.cost() < 0.98 * best.cost()) {
             best = t;
             have = true;
             gj_free(best_h);

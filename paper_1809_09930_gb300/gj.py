@@ -79,7 +79,8 @@ EXPORTS = ["gj_config_init", "gj_index_build", "gj_index_build_ex", "gj_self_joi
            "gj_self_join_part", "gj_index_get_info", "gj_last_join_stats", "gj_free",
            "gj_last_status", "gj_status_string", "gj_version", "gj_probe_fp64_tflops",
            "gj_kernel_launches", "gj_debug_tc_tile", "gj_self_join_noalloc", "gj_batch_build",
-           "gj_batch_self_join", "gj_batch_get_info", "gj_batch_free", "gj_autotune", "gj_batch_get_k"]
+           "gj_batch_self_join", "gj_batch_get_info", "gj_batch_free", "gj_autotune", "gj_batch_get_k",
+           "gj_neighbor_table"]
 
 _lib = None
 
@@ -135,6 +136,8 @@ def load(path: str | None = None):
     lib.gj_autotune.restype = C.c_int
     lib.gj_autotune.argtypes = [V, C.c_int64, C.c_int32, C.c_double, C.POINTER(gj_config),
                                 C.POINTER(gj_tune_result)]
+    lib.gj_neighbor_table.restype = C.c_int
+    lib.gj_neighbor_table.argtypes = [V, V, V, C.c_uint64, C.POINTER(C.c_uint64)]
     lib.gj_batch_get_k.restype = C.c_int
     lib.gj_batch_get_k.argtypes = [V, C.POINTER(C.c_int32)]
     if path is None:
@@ -236,6 +239,15 @@ def gj_self_join_part(h: int, part: int, nparts: int, out=None) -> tuple[int, in
     cnt = C.c_uint64(0)
     st = load().gj_self_join_part(h, int(part), int(nparts), p, cap, C.byref(cnt))
     del keep
+    return st, int(cnt.value)
+
+
+def gj_neighbor_table(h: int, row_start, nbr) -> tuple[int, int]:
+    """CSR neighbour table into CUDA tensors: row_start int64 (n+1,), nbr
+    int32/uint32 (cap,).  Returns (status, |R|)."""
+    cnt = C.c_uint64(0)
+    st = load().gj_neighbor_table(h, row_start.data_ptr(), nbr.data_ptr() if nbr is not None else None,
+                                  int(nbr.numel()) if nbr is not None else 0, C.byref(cnt))
     return st, int(cnt.value)
 
 
@@ -413,6 +425,18 @@ class Index:
         if st != GJ_OK:
             raise GJError(st, "gj_self_join (count)")
         return n
+
+    def neighbor_table(self):
+        """(row_start, nbr) as CUDA tensors (int64 (n+1,), int32 (|R|,))."""
+        import torch
+        n = self.info()["n"]
+        m = self.count()
+        row_start = torch.empty(n + 1, dtype=torch.int64, device="cuda")
+        nbr = torch.empty(max(m, 1), dtype=torch.int32, device="cuda")
+        st, c = gj_neighbor_table(self.h, row_start, nbr)
+        if st != GJ_OK:
+            raise GJError(st, "gj_neighbor_table")
+        return row_start, nbr[:c]
 
     def join(self, out=None, part: int | None = None, nparts: int = 1):
         """Pairs as a (|R|, 2) uint32 numpy array (or the given buffer's prefix)."""

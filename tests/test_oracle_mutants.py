@@ -101,3 +101,40 @@ def test_mutant_is_caught(name, tmp_path):
     finally:
         oracle._SRC = oracle._SRC_SAVED
         oracle._lib, oracle._LIB_PATH = saved_lib, saved_path
+
+
+# ---------------------------------------------------------------------------
+# constructNeighborTable (Python side of the oracle): mutants of the group-by
+# ---------------------------------------------------------------------------
+
+_real_table = oracle.neighbor_table
+
+
+def _table_value_order_only(pairs, n):
+    p = np.asarray(pairs, dtype=np.int64).reshape(-1, 2)
+    order = np.argsort(p[:, 1], kind="stable")          # forgets the key
+    counts = np.bincount(p[:, 0], minlength=n)
+    rs = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(counts, out=rs[1:])
+    return rs, p[order, 1].astype(np.uint32)
+
+
+def _table_inclusive_starts(pairs, n):
+    rs, nbr = _real_table(pairs, n)
+    return np.concatenate([rs[1:], rs[-1:]]), nbr      # row a starts one row late
+
+
+def _table_key_as_value(pairs, n):
+    rs, _ = _real_table(pairs, n)
+    p = np.asarray(pairs, dtype=np.int64).reshape(-1, 2)
+    order = np.lexsort((p[:, 1], p[:, 0]))
+    return rs, p[order, 0].astype(np.uint32)            # stores the key, not the value
+
+
+@pytest.mark.parametrize("mutant", [_table_value_order_only, _table_inclusive_starts, _table_key_as_value])
+def test_neighbor_table_pins_catch_mutants(mutant, monkeypatch):
+    from tests import test_oracle_pins as pins
+    pins.test_neighbor_table_rows_on_the_lattice(4, 3, 2)     # the real table passes
+    monkeypatch.setattr(oracle, "neighbor_table", mutant)
+    with pytest.raises(AssertionError):
+        pins.test_neighbor_table_rows_on_the_lattice(4, 3, 2)

@@ -225,3 +225,43 @@ def test_depth_stats_hand_example():
     assert (ds, pc) == (1 + 4, 2)
     ds, pc = oracle.depth_stats(X, 1.0, [3, 2, 1, 0], [0])
     assert (ds, pc) == (4 + 1, 2)
+
+
+# ---------------------------------------------------------------------------
+# constructNeighborTable (Alg. 1; Sec. 3.2.2) on the full integer lattice:
+# each row is known independently -- the lattice points x + o with integer
+# offsets |o|^2 <= E that stay inside the box, ids row-major
+# ---------------------------------------------------------------------------
+
+def lattice_row(x, L, E):
+    d = len(x)
+    r = int(math.isqrt(E))
+    offs = np.stack(np.meshgrid(*[np.arange(-r, r + 1)] * d, indexing="ij"), axis=-1).reshape(-1, d)
+    offs = offs[(offs * offs).sum(axis=1) <= E]
+    y = np.asarray(x) + offs
+    y = y[np.all((y >= 0) & (y < L), axis=1)]
+    ids = np.zeros(len(y), dtype=np.int64)
+    for j in range(d):
+        ids = ids * L + y[:, j]
+    return np.sort(ids)
+
+
+@pytest.mark.parametrize("L,d,E", [(4, 3, 2), (5, 2, 4), (3, 4, 1)])
+def test_neighbor_table_rows_on_the_lattice(L, d, E):
+    X = full_lattice(L, d)
+    n = len(X)
+    row_start, nbr = oracle.neighbor_table(oracle.brute(X, math.sqrt(E)), n)
+    assert row_start[0] == 0 and row_start[-1] == lattice_pairs_closed_form(L, d, E)
+    assert np.all(np.diff(row_start) >= 1)            # every point is its own neighbour
+    for a in range(n):
+        got = nbr[row_start[a]:row_start[a + 1]].astype(np.int64)
+        assert np.array_equal(got, lattice_row(X[a].astype(np.int64), L, E)), a
+
+
+def test_neighbor_table_empty_and_isolated_rows():
+    row_start, nbr = oracle.neighbor_table(np.zeros((0, 2), dtype=np.uint32), 3)
+    assert list(row_start) == [0, 0, 0, 0] and nbr.size == 0
+    X = np.array([[0.0], [10.0], [0.5], [20.0]])
+    row_start, nbr = oracle.neighbor_table(oracle.brute(X, 1.0), 4)
+    assert list(row_start) == [0, 2, 3, 5, 6]
+    assert list(nbr) == [0, 2, 1, 0, 2, 3]
