@@ -48,8 +48,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--form", choices=["plain", "tc"], default="tc")
-    ap.add_argument("--workload", choices=["paper", "jobs"], default="paper",
-                    help="paper: 2M uniform points per d; jobs: the 256 uneven jobs in one launch")
+    ap.add_argument("--workload", choices=["paper", "jobs", "exponential"], default="paper",
+                    help="paper: 2M uniform points per d; jobs: the 256 uneven jobs in one launch; "
+                         "exponential: the paper's own Syn16/32/64D2M shape (exponential, lambda = 40)")
     ap.add_argument("--no-plain", action="store_true",
                     help="skip the one-shot plain FP64 join of the d=16 set beside the tc form")
     ap.add_argument("--dims", default=None, help="comma list of d for the paper-scale workload")
@@ -145,7 +146,16 @@ def rank_sum(dist, xs: list, device: str = "cuda") -> list:
     return [int(v) for v in t.tolist()]
 
 
+# The paper's synthetic sets (Sec. 5.1: i.i.d. exponential, lambda = 40, 2e6
+# points) at the largest eps its Table 4 lists for each (Table 2 times
+# Syn16D2M at eps = 0.05).
+SYN_EPS = {16: 0.05, 32: 0.10, 64: 0.18}
+
+
 def workload_name(args, runs) -> str:
+    if args.workload == "exponential":
+        return (f"paper's Syn16/32/64D2M shape: exponential (lambda=40) [0,1]^d, n={args.n}, "
+                f"d in {[r['d'] for r in runs]}, eps {[r['eps'] for r in runs]} (Table 4)")
     return (f"paper-scale uniform [0,1)^d, n={args.n}, d in {[r['d'] for r in runs]}, "
             f"eps for 32 mean neighbours")
 
@@ -156,8 +166,11 @@ def workload(args):
     dims = [int(x) for x in (args.dims or ("16,32,64" if args.form == "tc" else "16")).split(",")]
     runs = []
     for d in dims:
+        if args.workload == "exponential":
+            runs.append(dict(d=d, n=args.n, eps=SYN_EPS[d], seed=4000 + d, kind="exponential", depth=None))
+            continue
         w = W[f"paper_d{d}"]
-        runs.append(dict(d=d, n=args.n, eps=w["eps"], seed=w["seed"],
+        runs.append(dict(d=d, n=args.n, eps=w["eps"], seed=w["seed"], kind="uniform",
                          depth=w.get("depth_per_pair")))
     return runs
 
@@ -172,7 +185,7 @@ def cpu_baseline(runs, budget_s=15.0):
     for r in runs:
         m = 8000
         while True:
-            X = synth.uniform(m, r["d"], r["seed"])
+            X = synth.generate(r["kind"], m, r["d"], r["seed"])
             t = time.perf_counter()
             st = oracle.grid_count(X, r["eps"], k=1)
             dt = time.perf_counter() - t
@@ -400,7 +413,7 @@ def main():
     # inputs resident in HBM before the timed region; outputs to a device buffer
     data = []
     for r in runs:
-        X = synth.uniform(r["n"], r["d"], r["seed"])
+        X = synth.generate(r["kind"], r["n"], r["d"], r["seed"])
         Xd = torch.from_numpy(X).to("cuda")
         data.append((r, X, Xd))
     torch.cuda.synchronize()

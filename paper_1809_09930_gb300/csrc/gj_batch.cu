@@ -302,6 +302,8 @@ gj_batch *build_batch(const gj_job *jobs, int32_t njobs, const gj_config &cfg, c
         J.e2 = h->e2;
         J.ew = h->ew;
         J.u = h->u;
+        J.d = h->info.d;
+        J.pad = 0;
         J.out = nullptr;
         J.cap = 0;
         if (e == cudaSuccess && h->tc_ready) {

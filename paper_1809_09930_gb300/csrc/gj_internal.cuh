@@ -129,6 +129,8 @@ struct TcJob {
     double e2, ew;       // fl(eps^2), SORTIDU window half-width
     int u;               // SORTIDU dimension or -1
     int Tbits;           // fp32 bits of the job's survivor threshold
+    int d;               // the job's own dimensions (the combined layout pads to the largest)
+    int pad;
     gj_pair *out;        // the job's device output (nullptr = count only)
     unsigned long long cap;
 };

@@ -123,3 +123,30 @@ def test_large_skewed_streamed_to_pinned_host():
     del t
     _check_properties(keys, w["n"])
     _check_queries(X, w["eps"], keys, _queries(w["n"], 55, m=32))
+
+
+def test_paper_syn16d2m_tc_sampled_queries():
+    """The paper's own Syn16D2M shape (Sec. 5.1: 2e6 exponential points,
+    lambda = 40, in 16-D) at eps = 0.05 (Table 2): dense co-located data, |R|
+    about 2.4e9.  The result stays on the device; each sampled query's list is
+    selected by a scan (no sort of the whole result)."""
+    n, d, eps = 2_000_000, 16, 0.05
+    X = synth.exponential(n, d, 4016)
+    Xd = torch.from_numpy(X).cuda()
+    with gj.Index(Xd, eps, k=0, flags=TC) as ix:
+        m = ix.count()
+        out = torch.empty((m, 2), dtype=torch.int32, device="cuda")
+        st, m2 = gj.gj_self_join(ix.h, out)
+    assert st == gj.GJ_OK and m2 == m
+    assert int((out[:, 0] == out[:, 1]).sum().item()) == n
+    e2 = eps * eps
+    for q in _queries(n, 16, m=24):
+        sel = out[:, 0] == q
+        got = np.sort(out[sel][:, 1].cpu().numpy().view(np.uint32))
+        ref = oracle.query_neighbors(X, eps, int(q))
+        for j in np.setxor1d(got, ref):
+            s = oracle.sqdist(X[q], X[int(j)])
+            assert abs(s - e2) <= TIE_REL * e2, f"query {q}: neighbour {j} differs"
+        # the reverse orientation of every listed pair is present too
+        rev = int(((out[:, 1] == q)).sum().item())
+        assert rev == got.size
