@@ -48,9 +48,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--form", choices=["plain", "tc"], default="tc")
-    ap.add_argument("--workload", choices=["paper", "jobs", "exponential"], default="paper",
+    ap.add_argument("--workload", choices=["paper", "jobs", "exponential", "qe"], default="paper",
                     help="paper: 2M uniform points per d; jobs: the 256 uneven jobs in one launch; "
-                         "exponential: the paper's own Syn16/32/64D2M shape (exponential, lambda = 40)")
+                         "exponential: the paper's own Syn16/32/64D2M shape (exponential, lambda = 40); "
+                         "qe: the similarity join Q join_eps E, 200k queries against the 2M d=16 set")
+    ap.add_argument("--nq", type=int, default=200_000, help="queries of the qe workload")
     ap.add_argument("--no-plain", action="store_true",
                     help="skip the one-shot plain FP64 join of the d=16 set beside the tc form")
     ap.add_argument("--dims", default=None, help="comma list of d for the paper-scale workload")
@@ -385,10 +387,91 @@ def bench_jobs(args):
     print(json.dumps(out), flush=True)
 
 
+def bench_qe(args):
+    """The similarity join Q join_eps E (Sec. 3.1): the 2M-point d = 16 set as
+    the entries (index built once, outside the timing), args.nq fresh uniform
+    queries; step = gj_join_qe into a device buffer.  Unit: query x entry
+    pairs in adjacent cells."""
+    import torch
+    from paper_1809_09930_gb300 import gj
+    with open(WORKLOADS) as f:
+        w = json.load(f)["paper_d16"]
+    steps = args.steps if args.steps is not None else 3
+    stream = torch.cuda.current_stream()
+    E = torch.from_numpy(synth.uniform(args.n, 16, w["seed"])).cuda()
+    Qh = synth.uniform(args.nq, 16, w["seed"] + 7919)
+    Q = torch.from_numpy(Qh).cuda()
+    ix = gj.Index(E, w["eps"], k=0, stream=stream.cuda_stream)
+    st, m = gj.gj_join_qe(ix.h, Q, None)
+    out = torch.empty((m + 16, 2), dtype=torch.int32, device="cuda")
+    for _ in range(args.warmup):
+        gj.gj_join_qe(ix.h, Q, out)
+    fp64 = gj.gj_probe_fp64_tflops()
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.synchronize()
+    clocks.start()
+    l0 = gj.gj_kernel_launches()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    join_ms, dims, cand = 0.0, 0, 0
+    for _ in range(steps):
+        st, m2 = gj.gj_join_qe(ix.h, Q, out)
+        if st != gj.GJ_OK or m2 != m:
+            raise RuntimeError(f"qe join: {gj.gj_status_string(st)}")
+        s = ix.stats()
+        join_ms += s["join_ms"]
+        dims += s["dims"]
+        cand += s["candidates"]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    launches = gj.gj_kernel_launches() - l0
+    ms = ev0.elapsed_time(ev1)
+    # end to end: host queries in, host pairs out (pinned)
+    hq = torch.from_numpy(Qh).pin_memory()
+    hout = torch.empty((m + 16, 2), dtype=torch.int32).pin_memory()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        gj.gj_join_qe(ix.h, hq, hout)
+    e2e_s = time.perf_counter() - t0
+    ix.close()
+    achieved = 3.0 * dims / (join_ms * 1e-3) / 1e12
+    peak = 0.75 * fp64
+    cb = None
+    if not args.no_baseline:
+        import oracle
+        mq = 2000
+        t = time.perf_counter()
+        oracle.brute_qe(Qh[:mq], E.cpu().numpy(), w["eps"])
+        dt = time.perf_counter() - t
+        cb = {"value": mq * args.n / dt, "unit": "distance evals/s", "cores": os.cpu_count(), "kind": "oracle",
+              "sample": f"nested loop of the first {mq} queries against all {args.n} entries, {dt:.1f} s"}
+    out_line = {
+        "metric": "distance evals/s (similarity join Q join_eps E, exact pair set)",
+        "value": cand / (ms * 1e-3), "unit": "distance evals/s", "n_gpus": 1, "steps": steps,
+        "warmup": args.warmup, "ms_per_step": ms / steps, "higher_is_better": True, "scaling": "strong",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"Q join_eps E: {args.nq} uniform queries x {args.n} uniform entries, d=16, "
+                               f"eps {w['eps']}", "pairs": m,
+                   "step": "gj_join_qe (query side build + one join launch) into a device buffer"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                     "traffic": None, "kernel": "k_join_plain (asymmetric)",
+                     "peak_source": "FP64 FMA probe measured in this run x 3/4 (DADD+DFMA mix)"},
+        "cpu_baseline": cb,
+        "e2e": {"value": cand / e2e_s, "unit": "distance evals/s", "h2d_bytes_per_step": int(Qh.nbytes),
+                "d2h_bytes_per_step": 8 * m},
+        "gpu_launches": int(launches), "clocks": clk,
+    }
+    print(json.dumps(out_line), flush=True)
+
+
 def main():
     args = parse()
     if args.workload == "jobs" and args.impl == "ours":
         bench_jobs(args)
+        return
+    if args.workload == "qe" and args.impl == "ours":
+        bench_qe(args)
         return
     runs = workload(args)
     if args.impl == "reference":

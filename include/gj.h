@@ -75,8 +75,9 @@ typedef struct {
     void    *stream;      /* cudaStream_t to run on; NULL = a stream the handle creates             */
     uint64_t batch_pairs; /* result batch size b_s in pairs; 0 = the rule of Sec. 3.2.2           */
     int32_t  device;      /* CUDA device ordinal; -1 = the calling thread's current device        */
-    int32_t  query_block; /* points per work item (query tile): 0 = default (120); 8..128, and
-                           * at most 120 with GJ_TC_FILTER (the 128-row tensor-core A tile)    */
+    int32_t  query_block; /* points per work item (query tile): 0 = default (120 points; the
+                           * tensor-core form: pieces of a cell between multiples of 128
+                           * sorted positions); 8..128, and at most 120 with GJ_TC_FILTER   */
     int32_t  tile;        /* plain form: candidate points staged per shared-memory tile,
                            * 0 = default (64 for d <= 32, else 32), 32 or 64                    */
     uint32_t reserved[5];
@@ -113,6 +114,7 @@ typedef struct {
     double   busy_ms;        /* join kernels: each CTA's start-to-exit time, averaged over the
                               * CTAs of a launch, summed over launches (the join's work spread
                               * evenly over the grid: its time without the tail)                  */
+    uint64_t candidates;     /* gj_join_qe: query x entry pairs in adjacent cells (its evals unit) */
 } gj_join_stats;
 
 /* Fill *cfg with defaults (k = 0, GJ_DEFAULT_FLAGS, own stream, paper batch rule). */
@@ -142,7 +144,7 @@ gj_index *gj_index_build_ex(const double *points, int64_t n, int32_t d, double e
 typedef struct {
     int32_t  k;            /* indexed dimensions                                              */
     uint32_t flags;        /* the input flags with GJ_TC_FILTER set or cleared by the pick     */
-    int32_t  query_block;  /* points per work item                                            */
+    int32_t  query_block;  /* gj_config.query_block of the pick (0 = the default blocks)      */
     int32_t  tile;         /* plain form: candidate tile (0 for the tensor-core form)         */
     uint64_t batch_pairs;  /* result batch size b_s for host output                           */
     uint64_t est_pairs;    /* |R| extrapolated from the trial join of the pick                */
@@ -160,10 +162,11 @@ typedef struct {
  * fixed, load-stratified share of the work items (one part of an entity
  * partition, Sec. 6.2; the part sized so that a trial's join takes about
  * 40 ms), extrapolated to the whole queue; the setting with the least build +
- * join time wins (by at least 2 %, else the earlier setting stays).  k runs over 1..min(d, 8) (1..3 for the
- * tensor-core form), the plain tiles over query blocks {120, 64} x candidate
- * tiles {64, 32}.  With GJ_TUNE_FORM in cfg->flags both forms are tried,
- * else only the form cfg->flags names.  The result batch size b_s is then
+ * join time wins (by at least 2 %, else the earlier setting stays).  k runs
+ * over 1..min(d, 8) (1..3 for the tensor-core form), then the query block
+ * over {default, 64} and the plain candidate tile over {64, 32}.  With
+ * GJ_TUNE_FORM in cfg->flags both forms are tried, else only the form
+ * cfg->flags names.  The result batch size b_s is then
  * chosen from the trial's |R| estimate, a timed device-to-host copy and the
  * measured per-launch overhead, so that the drain of each batch hides under
  * the join of the next (at least 3 batches, Sec. 3.2.2).
@@ -200,6 +203,28 @@ int gj_self_join(gj_index *h, gj_pair *pairs_out, uint64_t cap, uint64_t *count)
  */
 int gj_self_join_part(gj_index *h, int32_t part, int32_t nparts, gj_pair *pairs_out,
                       uint64_t cap, uint64_t *count);
+
+/*
+ * The similarity join Q join_eps E (Sec. 3.1; the self-join is the case
+ * Q = E): every pair (q, e) of a query row q and an entry row e with
+ * dist(q, e) <= eps, one orientation, q indexing the queries and e the rows
+ * the index h was built from (the entries, E).  The queries are keyed into
+ * E's grid (its REORDER permutation, cell width and origin), sorted by cell
+ * and by E's SORTIDU dimension; each query cell searches all adjacent
+ * non-empty entry cells; distances are the FP64 SHORTC sums of the self-join.
+ *   h          an index over E (any flags; the join uses the plain FP64 form)
+ *   queries    row-major nq x d FP64 (d = E's), host or device memory;
+ *              copied, the caller keeps ownership
+ *   pairs_out  host or device memory for cap pairs (a = query row, b = entry
+ *              row); NULL with cap == 0 counts only
+ *   count      out: |Q join_eps E|
+ * One kernel launch writes the pairs and counts them.  Returns GJ_OK;
+ * GJ_ERR_CAPACITY when the result exceeds cap (*count holds its size; the
+ * buffer holds an unspecified cap of them); GJ_ERR_NONFINITE for a NaN or
+ * infinite query coordinate; or another error code.  The eps is the index's.
+ */
+int gj_join_qe(gj_index *h, const double *queries, int64_t nq, gj_pair *pairs_out, uint64_t cap,
+               uint64_t *count);
 
 /*
  * The neighbour table (Alg. 1, constructNeighborTable; Sec. 3.2.2: the

@@ -8,6 +8,7 @@ marshals numpy arrays into it.
 
 Functions (paper section each follows):
   brute(X, eps)                     nested-loop join, the definition (Sec. 3.1)
+  brute_qe(Q, E, eps)               the similarity join Q join_eps E by its definition (Sec. 3.1)
   grid_join(X, eps, k, ...)         the paper's method on the CPU (Sec. 3.2.1, 4.1–4.4, Alg. 1)
   query_neighbors(X, eps, q)        neighbours of one point by the definition
   variance / reorder_perm           REORDER (Sec. 4.2)
@@ -66,6 +67,8 @@ def _load():
         lib.gjo_sqdist.argtypes = [P, P, C.c_int]
         lib.gjo_brute.restype = C.c_int64
         lib.gjo_brute.argtypes = [P, C.c_int64, C.c_int, C.c_double, P, C.c_int64, C.c_int]
+        lib.gjo_brute_qe.restype = C.c_int64
+        lib.gjo_brute_qe.argtypes = [P, C.c_int64, P, C.c_int64, C.c_int, C.c_double, P, C.c_int64, C.c_int]
         lib.gjo_query_neighbors.restype = C.c_int64
         lib.gjo_query_neighbors.argtypes = [P, C.c_int64, C.c_int, C.c_double, C.c_int64,
                                             P, C.c_int64]
@@ -135,6 +138,21 @@ def brute(X, eps: float, nthreads: int | None = None) -> np.ndarray:
     return _run_pairs(lambda buf, cap: lib.gjo_brute(X.ctypes.data, n, d, float(eps),
                                                      buf.ctypes.data, cap, _threads(nthreads)),
                       8 * n + 1024)
+
+
+def brute_qe(Q, E, eps: float, nthreads: int | None = None) -> np.ndarray:
+    """Q join_eps E (Sec. 3.1): every (q, e), q a row of Q and e a row of E,
+    within eps, by the nested loop; sorted by (q, e)."""
+    Q = _f64(Q)
+    E = _f64(E)
+    nq, d = Q.shape
+    if E.shape[1] != d:
+        raise ValueError("Q and E differ in dimension")
+    ne = E.shape[0]
+    lib = _load()
+    return _run_pairs(lambda buf, cap: lib.gjo_brute_qe(Q.ctypes.data, nq, E.ctypes.data, ne, d, float(eps),
+                                                        buf.ctypes.data, cap, _threads(nthreads)),
+                      4 * (nq + ne) + 1024)
 
 
 def brute_count(X, eps: float, nthreads: int | None = None) -> int:

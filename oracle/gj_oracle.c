@@ -19,6 +19,7 @@
  *
  * Two routes to R live here:
  *   gjo_brute      -- the nested-loop join of Sec. 3.1 (O(n^2)), the definition.
+ *   gjo_brute_qe   -- the same definition for two sets, Q join_eps E (Sec. 3.1).
  *   gjo_grid_join  -- the paper's method, steps in the paper's order:
  *                     REORDER (Sec. 4.2), grid index on the first k reordered
  *                     dimensions (Sec. 3.2.1, 4.1), 3^k adjacent-cell search
@@ -175,6 +176,64 @@ int64_t gjo_brute(const double *X, int64_t n, int d, double eps, uint64_t *out,
         args[t].lo = n * t / nthreads;
         args[t].hi = n * (t + 1) / nthreads;
         pthread_create(&th[t], NULL, brute_worker, &args[t]);
+    }
+    for (int t = 0; t < nthreads; ++t) {
+        pthread_join(th[t], NULL);
+        lists[t] = args[t].out;
+    }
+    int oom = 0;
+    int64_t total = gather(lists, nthreads, out, cap, &oom);
+    free(args);
+    free(th);
+    free(lists);
+    return oom ? -1 : total;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Similarity join Q join_eps E (Sec. 3.1: the self-join is the case Q = E).   */
+/* ------------------------------------------------------------------------- */
+
+typedef struct {
+    const double *Q, *E;
+    int64_t ne, lo, hi;
+    int d;
+    double e2;
+    keyvec out;
+} qe_arg;
+
+static void *qe_worker(void *p)
+{
+    qe_arg *a = (qe_arg *)p;
+    for (int64_t i = a->lo; i < a->hi; ++i)
+        for (int64_t j = 0; j < a->ne; ++j)
+            if (gjo_sqdist(a->Q + i * a->d, a->E + j * a->d, a->d) <= a->e2)
+                kv_push(&a->out, ((uint64_t)i << 32) | (uint64_t)j);
+    return NULL;
+}
+
+/* Every pair (q, e) of a row q of Q and a row e of E with s(q, e) <= fl(eps^2),
+ * as keys (q<<32 | e), ascending: the nested loop over Q x E.  Returns the
+ * count (writes at most cap keys), or -1 when memory ran out. */
+int64_t gjo_brute_qe(const double *Q, int64_t nq, const double *E, int64_t ne, int d, double eps,
+                     uint64_t *out, int64_t cap, int nthreads)
+{
+    if (nthreads < 1)
+        nthreads = 1;
+    if (nthreads > nq && nq > 0)
+        nthreads = (int)nq;
+    double e2 = eps * eps;
+    qe_arg *args = (qe_arg *)calloc((size_t)nthreads, sizeof(qe_arg));
+    pthread_t *th = (pthread_t *)calloc((size_t)nthreads, sizeof(pthread_t));
+    keyvec *lists = (keyvec *)calloc((size_t)nthreads, sizeof(keyvec));
+    for (int t = 0; t < nthreads; ++t) {
+        args[t].Q = Q;
+        args[t].E = E;
+        args[t].ne = ne;
+        args[t].d = d;
+        args[t].e2 = e2;
+        args[t].lo = nq * t / nthreads;
+        args[t].hi = nq * (t + 1) / nthreads;
+        pthread_create(&th[t], NULL, qe_worker, &args[t]);
     }
     for (int t = 0; t < nthreads; ++t) {
         pthread_join(th[t], NULL);

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libgj.so")
-SOURCES = ["gj_index.cu", "gj_join.cu", "gj_tc.cu", "gj_api.cu", "gj_noalloc.cu", "gj_batch.cu", "gj_tune.cu", "gj_table.cu"]
+SOURCES = ["gj_index.cu", "gj_join.cu", "gj_tc.cu", "gj_api.cu", "gj_noalloc.cu", "gj_batch.cu", "gj_tune.cu", "gj_table.cu", "gj_qjoin.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

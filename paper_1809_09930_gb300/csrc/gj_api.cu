@@ -31,6 +31,20 @@ static std::atomic<unsigned long long> g_launches{0};
 
 namespace gj {
 void set_last_status(int st) { t_last_status = st; }
+
+void pool_keep(int device)
+{
+    static std::atomic<uint64_t> done{0};
+    if (device < 0 || device >= 64 || (done.load() >> device) & 1u)
+        return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+        uint64_t keep = (uint64_t)8 << 30;   // freed index memory up to 8 GiB stays with the pool
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    cudaGetLastError();
+    done.fetch_or((uint64_t)1 << device);
+}
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 unsigned long long launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
 }  // namespace gj
@@ -245,6 +259,8 @@ int join_impl(gj_index *h, int part, int nparts, gj_pair *pairs_out, uint64_t ca
     TRYC(cudaGetLastError());
     uint64_t estimate = 0;
     const bool want_batches = !count_only_call && !dev_out;
+    if (want_batches && !h->drain_stream)
+        TRYC(cudaStreamCreateWithFlags(&h->drain_stream, cudaStreamNonBlocking));
     const int64_t S = std::max<int64_t>(1, std::min<int64_t>(100, nq / std::max(1, grid)));
     if (want_batches && h->cfg.batch_pairs == 0 && S >= 8) {
         const int64_t ns = (nq + S - 1) / S;
@@ -385,7 +401,7 @@ int join_impl(gj_index *h, int part, int nparts, gj_pair *pairs_out, uint64_t ca
         if (head >= qlimit && batch + 1 < nb)
             ++batch;
     }
-    if (st == GJ_OK)
+    if (st == GJ_OK && h->drain_stream)
         TRYC(cudaStreamSynchronize(h->drain_stream));
     TRYC(cudaStreamSynchronize(s));
 #undef TRYC
@@ -474,6 +490,7 @@ gj_index *gj_index_build_ex(const double *points, int64_t n, int32_t d, double e
         return nullptr;
     }
     h->device = dev;
+    pool_keep(dev);
     h->cfg = cfg;
     h->sms = prop.multiProcessorCount;
     h->info.n = n;
@@ -497,14 +514,10 @@ gj_index *gj_index_build_ex(const double *points, int64_t n, int32_t d, double e
             goto fail;
         }
     }
-    e = cudaStreamCreateWithFlags(&h->drain_stream, cudaStreamNonBlocking);
-    if (e != cudaSuccess) {
-        st = cuda_status(e);
-        goto fail;
-    }
-    e = cudaMalloc(&P, std::max<size_t>((size_t)n * d, 1) * sizeof(double));
+    // (the drain stream of host-output joins is made by the first such join)
+    e = dev_alloc(&P, std::max<size_t>((size_t)n * d, 1) * sizeof(double), h->stream);
     if (e == cudaSuccess)
-        e = cudaMalloc(&flag, sizeof(unsigned int));
+        e = dev_alloc(&flag, sizeof(unsigned int), h->stream);
     if (e == cudaSuccess)
         e = cudaMemsetAsync(flag, 0, sizeof(unsigned int), h->stream);
     if (e == cudaSuccess && n > 0)
@@ -526,13 +539,13 @@ gj_index *gj_index_build_ex(const double *points, int64_t n, int32_t d, double e
     st = build_index(h, P, n, d, eps, cfg.k, cfg.flags, h->stream);
     if (st != GJ_OK)
         goto fail;
-    cudaFree(P);
-    cudaFree(flag);
+    dev_free(P, h->stream);
+    dev_free(flag, h->stream);
     t_last_status = GJ_OK;
     return h;
 fail:
-    cudaFree(P);
-    cudaFree(flag);
+    dev_free(P, h->stream);
+    dev_free(flag, h->stream);
     gj_free(h);
     cudaGetLastError();
     t_last_status = st;
@@ -585,19 +598,21 @@ void gj_free(gj_index *h)
     if (!h)
         return;
     cudaSetDevice(h->device);
-    if (h->stream)
-        cudaStreamSynchronize(h->stream);
-    cudaFree(h->X);
-    cudaFree(h->orig);
-    cudaFree(h->cell_start);
-    cudaFree(h->cell_id);
-    cudaFree(h->adj_start);
-    cudaFree(h->adj);
-    cudaFree(h->items);
-    cudaFree(h->order);
-    cudaFree(h->XA);
-    cudaFree(h->XB);
-    cudaFree(h->tc_centre);
+    // index memory is returned to the pool in stream order: after the work
+    // already queued on the handle's stream, without waiting here
+    const cudaStream_t s = h->stream;
+    dev_free(h->X, s);
+    dev_free(h->orig, s);
+    dev_free(h->cell_start, s);
+    dev_free(h->cell_id, s);
+    dev_free(h->adj_start, s);
+    dev_free(h->adj, s);
+    dev_free(h->items, s);
+    dev_free(h->order, s);
+    dev_free(h->XA, s);
+    dev_free(h->XB, s);
+    dev_free(h->tc_centre, s);
+    dev_free(h->perm_dev, s);
     if (h->drain_stream)
         cudaStreamDestroy(h->drain_stream);
     if (h->own_stream && h->stream)

@@ -213,7 +213,9 @@ gj_batch *build_batch(const gj_job *jobs, int32_t njobs, const gj_config &cfg, c
     jc.device = dev;
     int64_t G_total = 0, A_total = 0, I_total = 0;
     jc.flags &= ~(GJ_AUTOTUNE | GJ_TUNE_FORM);
-    jc.query_block = 0;
+    // fixed 120-point blocks: a job's positions are shifted in the combined
+    // layout, so blocks aligned within the job would not stay aligned
+    jc.query_block = QB_TC;
     jc.tile = 0;
     for (int32_t j = 0; j < njobs && st == GJ_OK; ++j) {
         jc.k = ks[j];
@@ -230,15 +232,8 @@ gj_batch *build_batch(const gj_job *jobs, int32_t njobs, const gj_config &cfg, c
     std::vector<int64_t> A_j(njobs, 0);
     if (st == GJ_OK) {
         for (int32_t j = 0; j < njobs; ++j) {
-            int64_t na = 0;
-            if (hs[j]->G > 0)
-                e = cudaMemcpyAsync(&na, hs[j]->adj_start + hs[j]->G, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
-            if (e == cudaSuccess)
-                e = cudaStreamSynchronize(s);
-            if (e != cudaSuccess)
-                break;
-            A_j[j] = na;
-            A_total += na;
+            A_j[j] = hs[j]->G > 0 ? hs[j]->nadj : 0;
+            A_total += A_j[j];
         }
         st = cuda_status(e);
     }
@@ -312,8 +307,6 @@ gj_batch *build_batch(const gj_job *jobs, int32_t njobs, const gj_config &cfg, c
         } else {
             J.Tbits = 0;   // an empty job: nothing survives
         }
-        if (e == cudaSuccess)
-            e = cudaStreamSynchronize(s);
         st = cuda_status(e);
         P += n;
         C += h->G;

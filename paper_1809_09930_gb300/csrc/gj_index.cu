@@ -579,19 +579,80 @@ __global__ void k_adjacent(const int64_t *__restrict__ cell_id, const int64_t *_
     }
 }
 
+// Similarity join: the entry cells adjacent to each query cell (all of them,
+// no symmetry), one warp per query cell.  mode 0: count and sum the entry
+// cells' sizes; mode 1: write the list.
+__global__ void k_adjacent_qe(const int64_t *__restrict__ qcell_id, int64_t Gq, const int64_t *__restrict__ cell_id,
+                              const int64_t *__restrict__ cell_start, int64_t G, AdjParams a, int mode,
+                              int64_t *__restrict__ cnt, int64_t *__restrict__ nbsum,
+                              const int64_t *__restrict__ adj_start, uint32_t *__restrict__ adj)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t c = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (c >= Gq)
+        return;
+    const int64_t id = qcell_id[c];
+    int64_t coord[MAXK];
+    for (int j = 0; j < a.k; ++j)
+        coord[j] = (id / a.stride[j]) % a.nc[j];
+    int64_t found = 0, sz = 0;
+    const int64_t out = mode ? adj_start[c] : 0;
+    for (int64_t t0 = 0; t0 < a.pow3; t0 += 32) {
+        const int64_t t = t0 + lane;
+        int64_t b = -1;
+        if (t < a.pow3) {
+            int64_t r = t, nid = 0;
+            bool ok = true;
+            for (int j = a.k - 1; j >= 0; --j) {
+                const int64_t cj = coord[j] + (r % 3) - 1;
+                r /= 3;
+                ok &= (cj >= 0 && cj < a.nc[j]);
+                nid += cj * a.stride[j];
+            }
+            if (ok)
+                b = find_id(cell_id, G, nid);
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, b >= 0);
+        if (b >= 0) {
+            if (mode)
+                adj[out + found + __popc(m & ((1u << lane) - 1u))] = (uint32_t)b;
+            else
+                sz += cell_start[b + 1] - cell_start[b];
+        }
+        found += __popc(m);
+    }
+    if (!mode) {
+        for (int o = 16; o; o >>= 1)
+            sz += __shfl_xor_sync(0xffffffffu, sz, o);
+        if (lane == 0) {
+            cnt[c] = found;
+            nbsum[c] = sz;
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Work items
 // ---------------------------------------------------------------------------
-__global__ void k_item_counts(const int64_t *__restrict__ cell_start, int64_t G, int qb, int64_t *__restrict__ cnt)
+// Items of a cell: blocks of qb points from the cell's start, or (align > 0)
+// the pieces of the cell between multiples of align in sorted position, so
+// that every block but a cell's first starts on a multiple of align.
+__global__ void k_item_counts(const int64_t *__restrict__ cell_start, int64_t G, int qb, int align,
+                              int64_t *__restrict__ cnt)
 {
     int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (c < G)
-        cnt[c] = (cell_start[c + 1] - cell_start[c] + qb - 1) / qb;
+    if (c < G) {
+        const int64_t s = cell_start[c], e = cell_start[c + 1];
+        if (align > 0)
+            cnt[c] = e > s ? (e - 1) / align - s / align + 1 : 0;
+        else
+            cnt[c] = (e - s + qb - 1) / qb;
+    }
 }
 
 // items of cell c at [istart[c], ...); cost key = ~float bits of the load
 // estimate (ascending key = descending load); also sums candidate pairs.
-__global__ void k_items(const int64_t *__restrict__ cell_start, int64_t G, int qb,
+__global__ void k_items(const int64_t *__restrict__ cell_start, int64_t G, int qb, int align,
                         const int64_t *__restrict__ istart, const int64_t *__restrict__ nbsum,
                         Item *__restrict__ items, uint64_t *__restrict__ key, uint32_t *__restrict__ val,
                         unsigned long long *__restrict__ cand)
@@ -602,15 +663,41 @@ __global__ void k_items(const int64_t *__restrict__ cell_start, int64_t G, int q
     const int64_t s = cell_start[c], e = cell_start[c + 1], len = e - s;
     const int64_t nb = nbsum[c];
     int64_t it = istart[c];
-    for (int64_t q = s; q < e; q += qb, ++it) {
-        uint32_t ql = (uint32_t)min((int64_t)qb, e - q);
+    for (int64_t q = s; q < e; ++it) {
+        const int64_t qe = align > 0 ? min(e, (q / align + 1) * align) : min(e, q + qb);
+        const uint32_t ql = (uint32_t)(qe - q);
         items[it] = Item{(uint32_t)c, (uint32_t)q, ql, 0u};
         float load = (float)ql * (float)(nb + (e - q));
         key[it] = (uint64_t)(~__float_as_uint(load));
         val[it] = (uint32_t)it;
+        q = qe;
     }
     unsigned long long pairs = (unsigned long long)(len * (len - 1) / 2) + (unsigned long long)(len * nb);
     atomicAdd(cand, pairs);
+}
+
+// Similarity join: query blocks of qb points per query cell; load = block
+// size x points of the adjacent entry cells; candidate pairs = |Q cell| x
+// points of the adjacent entry cells.
+__global__ void k_qe_items(const int64_t *__restrict__ qcell_start, int64_t Gq, int qb,
+                           const int64_t *__restrict__ istart, const int64_t *__restrict__ nbsum,
+                           Item *__restrict__ items, uint64_t *__restrict__ key, uint32_t *__restrict__ val,
+                           unsigned long long *__restrict__ cand)
+{
+    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c >= Gq)
+        return;
+    const int64_t s = qcell_start[c], e = qcell_start[c + 1];
+    const int64_t nb = nbsum[c];
+    int64_t it = istart[c];
+    for (int64_t q = s; q < e; q += qb, ++it) {
+        const uint32_t ql = (uint32_t)min((int64_t)qb, e - q);
+        items[it] = Item{(uint32_t)c, (uint32_t)q, ql, 0u};
+        const float load = (float)ql * (float)nb;
+        key[it] = (uint64_t)(~__float_as_uint(load));
+        val[it] = (uint32_t)it;
+    }
+    atomicAdd(cand, (unsigned long long)((e - s) * nb));
 }
 
 // ---------------------------------------------------------------------------
@@ -675,8 +762,8 @@ int build_index(gj_index *h, const double *P, int64_t n, int d, double eps, int 
         h->npad = 32;
 
     // (a) REORDER statistics
-    GJ_TRY(cudaMalloc(&part, ((size_t)nblk_stats * d * 3 + d) * sizeof(double)));
-    GJ_TRY(cudaMalloc(&stats, (size_t)d * 4 * sizeof(double)));
+    GJ_TRY(dev_alloc(&part, ((size_t)nblk_stats * d * 3 + d) * sizeof(double), s));
+    GJ_TRY(dev_alloc(&stats, (size_t)d * 4 * sizeof(double), s));
     if (n > 0) {
         GJ_TRY(launch_dim_stats(P, n, d, part, nblk_stats, stats, s));
         GJ_TRY(cudaMemcpyAsync(hs.data(), stats, (size_t)d * 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -716,7 +803,10 @@ int build_index(gj_index *h, const double *P, int64_t n, int d, double eps, int 
                 invw_all[j] = 0.0;
         }
         const bool tc = (flags & GJ_TC_FILTER) && ((d + 4 + 15) / 16) * 16 <= 128;
-        h->qb = tc ? QB_TC : QB_PLAIN;
+        // tensor-core form, default blocks: pieces of a cell between multiples of
+        // 128 positions, so that the 128-row A tile starts at the block itself
+        h->q_align = (tc && h->cfg.query_block == 0) ? QB : 0;
+        h->qb = h->q_align ? QB : (tc ? QB_TC : QB_PLAIN);
         if (h->cfg.query_block > 0)
             h->qb = std::min(h->cfg.query_block, tc ? QB_TC : QB);
         h->plain_ct = tc ? 0 : h->cfg.tile;
@@ -754,18 +844,27 @@ int build_index(gj_index *h, const double *P, int64_t n, int d, double eps, int 
         int bits = 0;
         while (bits < 63 && (((int64_t)1 << bits) < strd))
             ++bits;
+        h->grid_k = k;
+        h->grid_bits = bits;
+        for (int j = 0; j < MAXK; ++j) {
+            h->grid_perm[j] = j < k ? gp.perm[j] : 0;
+            h->grid_origin[j] = j < k ? gp.origin[j] : 0.0;
+            h->grid_invw[j] = j < k ? gp.invw[j] : 0.0;
+            h->grid_nc[j] = j < k ? gp.nc[j] : 1;
+            h->grid_stride[j] = j < k ? gp.stride[j] : 0;
+        }
         // SORTIDU dimension: first un-indexed reordered dimension (or 0 when k == d)
         h->u = (flags & GJ_SORTIDU) ? (k < d ? k : 0) : -1;
         h->info.sortidu_dim = h->u;
 
         // key buffers
         counts_cap = radix_counts_needed(maxn);
-        GJ_TRY(cudaMalloc(&k0, maxn * sizeof(uint64_t)));
-        GJ_TRY(cudaMalloc(&k1, maxn * sizeof(uint64_t)));
-        GJ_TRY(cudaMalloc(&v0, maxn * sizeof(uint32_t)));
-        GJ_TRY(cudaMalloc(&v1, maxn * sizeof(uint32_t)));
-        GJ_TRY(cudaMalloc(&counts, counts_cap * sizeof(uint32_t)));
-        GJ_TRY(cudaMalloc(&perm_dev, d * sizeof(int)));
+        GJ_TRY(dev_alloc(&k0, maxn * sizeof(uint64_t), s));
+        GJ_TRY(dev_alloc(&k1, maxn * sizeof(uint64_t), s));
+        GJ_TRY(dev_alloc(&v0, maxn * sizeof(uint32_t), s));
+        GJ_TRY(dev_alloc(&v1, maxn * sizeof(uint32_t), s));
+        GJ_TRY(dev_alloc(&counts, counts_cap * sizeof(uint32_t), s));
+        GJ_TRY(dev_alloc(&perm_dev, d * sizeof(int), s));
         GJ_TRY(cudaMemcpyAsync(perm_dev, perm.data(), d * sizeof(int), cudaMemcpyHostToDevice, s));
 
         if (n > 0) {
@@ -789,8 +888,8 @@ int build_index(gj_index *h, const double *P, int64_t n, int d, double eps, int 
         }
 
         // sorted SoA points
-        GJ_TRY(cudaMalloc(&h->X, (size_t)d * h->npad * sizeof(double)));
-        GJ_TRY(cudaMalloc(&h->orig, maxn * sizeof(uint32_t)));
+        GJ_TRY(dev_alloc(&h->X, (size_t)d * h->npad * sizeof(double), s));
+        GJ_TRY(dev_alloc(&h->orig, maxn * sizeof(uint32_t), s));
         GJ_TRY(cudaMemsetAsync(h->X, 0, (size_t)d * h->npad * sizeof(double), s));
         if (n > 0) {
             note_launch();
@@ -800,8 +899,8 @@ int build_index(gj_index *h, const double *P, int64_t n, int d, double eps, int 
 
         // (b) non-empty cells
         tmp_cap = scan_tmp_needed(maxn) + 64;
-        GJ_TRY(cudaMalloc(&tmp, tmp_cap * sizeof(int64_t)));
-        GJ_TRY(cudaMalloc(&flagbuf, (maxn + 1) * sizeof(int64_t)));
+        GJ_TRY(dev_alloc(&tmp, tmp_cap * sizeof(int64_t), s));
+        GJ_TRY(dev_alloc(&flagbuf, (maxn + 1) * sizeof(int64_t), s));
         if (n > 0) {
             note_launch();
             k_heads<<<(int)grid_blocks(n, 256), 256, 0, s>>>(k0, n, flagbuf);
@@ -814,8 +913,8 @@ int build_index(gj_index *h, const double *P, int64_t n, int d, double eps, int 
             G = last_pre + last_flag;
         }
         h->G = G;
-        GJ_TRY(cudaMalloc(&h->cell_start, (G + 1) * sizeof(int64_t)));
-        GJ_TRY(cudaMalloc(&h->cell_id, std::max<int64_t>(G, 1) * sizeof(int64_t)));
+        GJ_TRY(dev_alloc(&h->cell_start, (G + 1) * sizeof(int64_t), s));
+        GJ_TRY(dev_alloc(&h->cell_id, std::max<int64_t>(G, 1) * sizeof(int64_t), s));
         if (n > 0) {
             note_launch();
             k_cells<<<(int)grid_blocks(n, 256), 256, 0, s>>>(k0, n, flagbuf, h->cell_start, h->cell_id);
@@ -828,9 +927,9 @@ int build_index(gj_index *h, const double *P, int64_t n, int d, double eps, int 
         }
 
         // (c) adjacency
-        GJ_TRY(cudaMalloc(&cnt, (G + 1) * sizeof(int64_t)));
-        GJ_TRY(cudaMalloc(&nbsum, std::max<int64_t>(G, 1) * sizeof(int64_t)));
-        GJ_TRY(cudaMalloc(&h->adj_start, (G + 1) * sizeof(int64_t)));
+        GJ_TRY(dev_alloc(&cnt, (G + 1) * sizeof(int64_t), s));
+        GJ_TRY(dev_alloc(&nbsum, std::max<int64_t>(G, 1) * sizeof(int64_t), s));
+        GJ_TRY(dev_alloc(&h->adj_start, (G + 1) * sizeof(int64_t), s));
         if (G > 0) {
             int64_t thr = G * 32;
             note_launch();
@@ -844,9 +943,10 @@ int build_index(gj_index *h, const double *P, int64_t n, int d, double eps, int 
             GJ_TRY(cudaMemcpyAsync(&last_pre, h->adj_start + G - 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
             GJ_TRY(cudaStreamSynchronize(s));
             nadj = last_pre + last_cnt;
+            h->nadj = nadj;
             note_launch();
             k_set_i64<<<1, 1, 0, s>>>(h->adj_start + G, nadj);
-            GJ_TRY(cudaMalloc(&h->adj, std::max<int64_t>(nadj, 1) * sizeof(uint32_t)));
+            GJ_TRY(dev_alloc(&h->adj, std::max<int64_t>(nadj, 1) * sizeof(uint32_t), s));
             note_launch();
             k_adjacent<<<(int)grid_blocks(thr, 256), 256, 0, s>>>(h->cell_id, h->cell_start, G, ap, 1, nullptr,
                                                                   nullptr, h->adj_start, h->adj);
@@ -854,15 +954,15 @@ int build_index(gj_index *h, const double *P, int64_t n, int d, double eps, int 
         } else {
             note_launch();
             k_set_i64<<<1, 1, 0, s>>>(h->adj_start, 0);
-            GJ_TRY(cudaMalloc(&h->adj, sizeof(uint32_t)));
+            GJ_TRY(dev_alloc(&h->adj, sizeof(uint32_t), s));
         }
 
         // (e) items, ordered by descending load
-        GJ_TRY(cudaMalloc(&cand_dev, sizeof(unsigned long long)));
+        GJ_TRY(dev_alloc(&cand_dev, sizeof(unsigned long long), s));
         GJ_TRY(cudaMemsetAsync(cand_dev, 0, sizeof(unsigned long long), s));
         if (G > 0) {
             note_launch();
-            k_item_counts<<<(int)grid_blocks(G, 256), 256, 0, s>>>(h->cell_start, G, h->qb, cnt);
+            k_item_counts<<<(int)grid_blocks(G, 256), 256, 0, s>>>(h->cell_start, G, h->qb, h->q_align, cnt);
             int64_t last_cnt = 0, last_pre = 0;
             GJ_TRY(cudaMemcpyAsync(&last_cnt, cnt + G - 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
             GJ_TRY(exclusive_scan_i64(cnt, G, tmp, tmp_cap, s));
@@ -871,15 +971,15 @@ int build_index(gj_index *h, const double *P, int64_t n, int d, double eps, int 
             nitems = last_pre + last_cnt;
         }
         h->nitems = nitems;
-        GJ_TRY(cudaMalloc(&h->items, std::max<int64_t>(nitems, 1) * sizeof(Item)));
-        GJ_TRY(cudaMalloc(&h->order, std::max<int64_t>(nitems, 1) * sizeof(uint32_t)));
+        GJ_TRY(dev_alloc(&h->items, std::max<int64_t>(nitems, 1) * sizeof(Item), s));
+        GJ_TRY(dev_alloc(&h->order, std::max<int64_t>(nitems, 1) * sizeof(uint32_t), s));
         if (nitems > 0) {
             if (nitems > maxn) {   // cannot happen (items <= points), guard the key buffers
                 st = GJ_ERR_CUDA;
                 goto done;
             }
             note_launch();
-            k_items<<<(int)grid_blocks(G, 256), 256, 0, s>>>(h->cell_start, G, h->qb, cnt, nbsum, h->items, k0, v0,
+            k_items<<<(int)grid_blocks(G, 256), 256, 0, s>>>(h->cell_start, G, h->qb, h->q_align, cnt, nbsum, h->items, k0, v0,
                                                              cand_dev);
             GJ_TRY(cudaGetLastError());
             GJ_TRY(radix_sort_pairs(k0, v0, k1, v1, nitems, 0, 32, counts, counts_cap, s));
@@ -899,19 +999,195 @@ int build_index(gj_index *h, const double *P, int64_t n, int d, double eps, int 
     h->info.work_items = nitems;
 
 done:
-    cudaFree(part);
-    cudaFree(stats);
-    cudaFree(k0);
-    cudaFree(k1);
-    cudaFree(v0);
-    cudaFree(v1);
-    cudaFree(counts);
-    cudaFree(flagbuf);
-    cudaFree(tmp);
-    cudaFree(cnt);
-    cudaFree(nbsum);
-    cudaFree(perm_dev);
-    cudaFree(cand_dev);
+    dev_free(part, s);
+    dev_free(stats, s);
+    dev_free(k0, s);
+    dev_free(k1, s);
+    dev_free(v0, s);
+    dev_free(v1, s);
+    dev_free(counts, s);
+    dev_free(flagbuf, s);
+    dev_free(tmp, s);
+    dev_free(cnt, s);
+    dev_free(nbsum, s);
+    if (st == GJ_OK && !h->perm_dev) {
+        h->perm_dev = perm_dev;   // kept: a similarity join gathers its queries with it
+        perm_dev = nullptr;
+    }
+    dev_free(perm_dev, s);
+    dev_free(cand_dev, s);
+    return st;
+}
+
+void free_query_side(QuerySide *qs, cudaStream_t s)
+{
+    dev_free(qs->XQ, s);
+    dev_free(qs->qorig, s);
+    dev_free(qs->qcell_start, s);
+    dev_free(qs->qcell_id, s);
+    dev_free(qs->adj_start, s);
+    dev_free(qs->adj, s);
+    dev_free(qs->items, s);
+    dev_free(qs->order, s);
+    *qs = QuerySide{};
+}
+
+// The query side of Q join_eps E over the entry index h: queries (device,
+// row-major nq x d, finite) keyed into the entry grid exactly as entries are
+// (cell_coord clamps a coordinate into [0, nc): a query within eps of an entry
+// is at most one cell away from it before the clamp, and clamping keeps it so),
+// sorted by (cell, u), gathered into the REORDER structure-of-arrays layout;
+// query cells, their adjacent entry cells, and load-ordered work items of at
+// most qb queries.
+int build_query_side(const gj_index *h, const double *Q, int64_t nq, int qb, QuerySide *qs, cudaStream_t s)
+{
+    int st = GJ_OK;
+    const int d = h->info.d;
+    const int64_t maxn = std::max<int64_t>(nq, 1);
+    uint64_t *k0 = nullptr, *k1 = nullptr;
+    uint32_t *v0 = nullptr, *v1 = nullptr, *counts = nullptr;
+    int64_t *flagbuf = nullptr, *tmp = nullptr, *cnt = nullptr, *nbsum = nullptr;
+    unsigned long long *cand_dev = nullptr;
+    int64_t Gq = 0, nitems = 0, nadj = 0;
+    GridParams gp{};
+    AdjParams ap{};
+    gp.k = h->grid_k;
+    gp.d = d;
+    ap.k = h->grid_k;
+    ap.pow3 = 1;
+    for (int j = 0; j < h->grid_k; ++j) {
+        gp.perm[j] = h->grid_perm[j];
+        gp.origin[j] = h->grid_origin[j];
+        gp.invw[j] = h->grid_invw[j];
+        gp.nc[j] = h->grid_nc[j];
+        gp.stride[j] = h->grid_stride[j];
+        ap.nc[j] = gp.nc[j];
+        ap.stride[j] = gp.stride[j];
+        ap.pow3 *= 3;
+    }
+    *qs = QuerySide{};
+    qs->nq = nq;
+    qs->qnpad = std::max<int64_t>(32, ((nq + 31) / 32) * 32);
+    const int64_t counts_cap = radix_counts_needed(maxn);
+    const int64_t tmp_cap = scan_tmp_needed(maxn + 1) + 64;
+    GJ_TRY(dev_alloc(&k0, maxn * sizeof(uint64_t), s));
+    GJ_TRY(dev_alloc(&k1, maxn * sizeof(uint64_t), s));
+    GJ_TRY(dev_alloc(&v0, maxn * sizeof(uint32_t), s));
+    GJ_TRY(dev_alloc(&v1, maxn * sizeof(uint32_t), s));
+    GJ_TRY(dev_alloc(&counts, counts_cap * sizeof(uint32_t), s));
+    GJ_TRY(dev_alloc(&tmp, tmp_cap * sizeof(int64_t), s));
+    GJ_TRY(dev_alloc(&flagbuf, (maxn + 1) * sizeof(int64_t), s));
+    GJ_TRY(dev_alloc(&cand_dev, sizeof(unsigned long long), s));
+    GJ_TRY(cudaMemsetAsync(cand_dev, 0, sizeof(unsigned long long), s));
+    // (1) keys: cell of the entry grid, then the SORTIDU coordinate inside a cell
+    if (nq > 0) {
+        if (h->u >= 0) {
+            note_launch();
+            k_ukeys<<<(int)grid_blocks(nq, 256), 256, 0, s>>>(Q, nq, d, h->info.perm[h->u], k0, v0);
+            GJ_TRY(cudaGetLastError());
+            GJ_TRY(radix_sort_pairs(k0, v0, k1, v1, nq, 0, 64, counts, counts_cap, s));
+            GJ_TRY(cudaMemcpyAsync(v1, v0, nq * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+            note_launch();
+            k_cellkeys<<<(int)grid_blocks(nq, 256), 256, 0, s>>>(Q, nq, gp, v1, k0, nullptr);
+        } else {
+            note_launch();
+            k_cellkeys<<<(int)grid_blocks(nq, 256), 256, 0, s>>>(Q, nq, gp, nullptr, k0, v0);
+        }
+        GJ_TRY(cudaGetLastError());
+        GJ_TRY(radix_sort_pairs(k0, v0, k1, v1, nq, 0, ((h->grid_bits + 7) / 8) * 8, counts, counts_cap, s));
+    }
+    // (2) queries in the reordered structure-of-arrays layout
+    GJ_TRY(dev_alloc(&qs->XQ, (size_t)d * qs->qnpad * sizeof(double), s));
+    GJ_TRY(dev_alloc(&qs->qorig, maxn * sizeof(uint32_t), s));
+    GJ_TRY(cudaMemsetAsync(qs->XQ, 0, (size_t)d * qs->qnpad * sizeof(double), s));
+    if (nq > 0) {
+        note_launch();
+        k_gather_soa<<<(int)grid_blocks(nq, 32), 256, 0, s>>>(Q, nq, d, qs->qnpad, v0, h->perm_dev, qs->XQ,
+                                                             qs->qorig);
+        GJ_TRY(cudaGetLastError());
+        // (3) query cells
+        note_launch();
+        k_heads<<<(int)grid_blocks(nq, 256), 256, 0, s>>>(k0, nq, flagbuf);
+        int64_t last_flag = 0, last_pre = 0;
+        GJ_TRY(cudaMemcpyAsync(&last_flag, flagbuf + nq - 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        GJ_TRY(exclusive_scan_i64(flagbuf, nq, tmp, tmp_cap, s));
+        GJ_TRY(cudaMemcpyAsync(&last_pre, flagbuf + nq - 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        GJ_TRY(cudaStreamSynchronize(s));
+        Gq = last_pre + last_flag;
+    }
+    qs->Gq = Gq;
+    GJ_TRY(dev_alloc(&qs->qcell_start, (Gq + 1) * sizeof(int64_t), s));
+    GJ_TRY(dev_alloc(&qs->qcell_id, std::max<int64_t>(Gq, 1) * sizeof(int64_t), s));
+    GJ_TRY(dev_alloc(&qs->adj_start, (Gq + 1) * sizeof(int64_t), s));
+    GJ_TRY(dev_alloc(&cnt, std::max<int64_t>(Gq, 1) * sizeof(int64_t), s));
+    GJ_TRY(dev_alloc(&nbsum, std::max<int64_t>(Gq, 1) * sizeof(int64_t), s));
+    note_launch();
+    k_set_i64<<<1, 1, 0, s>>>(qs->qcell_start + Gq, nq);
+    if (Gq > 0) {
+        note_launch();
+        k_cells<<<(int)grid_blocks(nq, 256), 256, 0, s>>>(k0, nq, flagbuf, qs->qcell_start, qs->qcell_id);
+        // (4) entry cells adjacent to each query cell
+        const int64_t thr = Gq * 32;
+        note_launch();
+        k_adjacent_qe<<<(int)grid_blocks(thr, 256), 256, 0, s>>>(qs->qcell_id, Gq, h->cell_id, h->cell_start, h->G,
+                                                                 ap, 0, cnt, nbsum, nullptr, nullptr);
+        GJ_TRY(cudaGetLastError());
+        GJ_TRY(cudaMemcpyAsync(qs->adj_start, cnt, Gq * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+        int64_t last_cnt = 0, last_pre = 0;
+        GJ_TRY(cudaMemcpyAsync(&last_cnt, cnt + Gq - 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        GJ_TRY(exclusive_scan_i64(qs->adj_start, Gq, tmp, tmp_cap, s));
+        GJ_TRY(cudaMemcpyAsync(&last_pre, qs->adj_start + Gq - 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        GJ_TRY(cudaStreamSynchronize(s));
+        nadj = last_pre + last_cnt;
+        note_launch();
+        k_set_i64<<<1, 1, 0, s>>>(qs->adj_start + Gq, nadj);
+        GJ_TRY(dev_alloc(&qs->adj, std::max<int64_t>(nadj, 1) * sizeof(uint32_t), s));
+        if (nadj > 0) {
+            note_launch();
+            k_adjacent_qe<<<(int)grid_blocks(thr, 256), 256, 0, s>>>(qs->qcell_id, Gq, h->cell_id, h->cell_start,
+                                                                     h->G, ap, 1, nullptr, nullptr, qs->adj_start,
+                                                                     qs->adj);
+            GJ_TRY(cudaGetLastError());
+        }
+        // (5) work items by descending load
+        note_launch();
+        k_item_counts<<<(int)grid_blocks(Gq, 256), 256, 0, s>>>(qs->qcell_start, Gq, qb, 0, cnt);
+        GJ_TRY(cudaMemcpyAsync(&last_cnt, cnt + Gq - 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        GJ_TRY(exclusive_scan_i64(cnt, Gq, tmp, tmp_cap, s));
+        GJ_TRY(cudaMemcpyAsync(&last_pre, cnt + Gq - 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        GJ_TRY(cudaStreamSynchronize(s));
+        nitems = last_pre + last_cnt;
+    } else {
+        GJ_TRY(dev_alloc(&qs->adj, sizeof(uint32_t), s));
+        note_launch();
+        k_set_i64<<<1, 1, 0, s>>>(qs->adj_start, 0);
+    }
+    qs->nitems = nitems;
+    GJ_TRY(dev_alloc(&qs->items, std::max<int64_t>(nitems, 1) * sizeof(Item), s));
+    GJ_TRY(dev_alloc(&qs->order, std::max<int64_t>(nitems, 1) * sizeof(uint32_t), s));
+    if (nitems > 0) {
+        note_launch();
+        k_qe_items<<<(int)grid_blocks(Gq, 256), 256, 0, s>>>(qs->qcell_start, Gq, qb, cnt, nbsum, qs->items,
+                                                             k0, v0, cand_dev);
+        GJ_TRY(cudaGetLastError());
+        GJ_TRY(radix_sort_pairs(k0, v0, k1, v1, nitems, 0, 32, counts, counts_cap, s));
+        GJ_TRY(cudaMemcpyAsync(qs->order, v0, nitems * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+    }
+    GJ_TRY(cudaMemcpyAsync(&qs->candidates, cand_dev, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    GJ_TRY(cudaStreamSynchronize(s));
+done:
+    dev_free(k0, s);
+    dev_free(k1, s);
+    dev_free(v0, s);
+    dev_free(v1, s);
+    dev_free(counts, s);
+    dev_free(flagbuf, s);
+    dev_free(tmp, s);
+    dev_free(cnt, s);
+    dev_free(nbsum, s);
+    dev_free(cand_dev, s);
+    if (st != GJ_OK)
+        free_query_side(qs, s);
     return st;
 }
 

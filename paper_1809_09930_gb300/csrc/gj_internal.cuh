@@ -75,6 +75,12 @@ struct IndexView {
     double e2;      // fl(eps*eps)
     double ew;      // SORTIDU window half-width (eps widened)
     int ct;         // plain form: candidate tile (32 or 64), 0 = by d
+    // similarity join Q join E (asym != 0): queries come from XQ/qorig, items and
+    // adjacency are the query side's, candidates the entries'; one orientation
+    int asym;
+    const double *XQ;
+    const uint32_t *qorig;
+    int64_t qnpad;
 };
 
 struct JoinLaunch {
@@ -91,6 +97,23 @@ struct JoinLaunch {
     gj_pair *staging;           // per-CTA staging areas
     uint32_t stg_cap;           // pairs per CTA
 };
+
+// Index memory comes from the device's stream-ordered pool: an allocation or
+// a free is queued on the build's stream and does not wait for the device
+// (a build of many small indices, as for a many-jobs batch, would otherwise
+// spend most of its time in the allocator).  pool_keep raises the pool's
+// release threshold so that freed blocks are reused instead of returned.
+template <class T>
+inline cudaError_t dev_alloc(T **p, size_t bytes, cudaStream_t s)
+{
+    return cudaMallocAsync(reinterpret_cast<void **>(p), bytes, s);
+}
+inline void dev_free(void *p, cudaStream_t s)
+{
+    if (p)
+        cudaFreeAsync(p, s);
+}
+void pool_keep(int device);
 
 // Count of kernels this library has launched (process-wide); read through
 // gj_kernel_launches().
@@ -150,6 +173,26 @@ cudaError_t launch_join_tc_jobs(const JoinLaunch &L, const void *XA, const void 
 cudaError_t tc_jobs_launch_attr(int Kp);
 void set_last_status(int st);
 
+// Query side of a similarity join Q join_eps E (gj_index.cu, gj_qjoin.cu): the
+// queries sorted into the entry index's grid, with their own cells, the
+// entry cells adjacent to each, and work items.
+struct QuerySide {
+    int64_t nq = 0, qnpad = 0;
+    double *XQ = nullptr;           // FP64 [d][qnpad]: queries in (cell, u) order, dimensions in REORDER order
+    uint32_t *qorig = nullptr;      // original query row of each sorted position
+    int64_t Gq = 0;
+    int64_t *qcell_start = nullptr; // [Gq + 1]
+    int64_t *qcell_id = nullptr;    // [Gq] entry-grid linear ids
+    int64_t *adj_start = nullptr;   // [Gq + 1] into adj
+    uint32_t *adj = nullptr;        // entry cells adjacent to each query cell
+    Item *items = nullptr;
+    uint32_t *order = nullptr;      // items by descending load
+    int64_t nitems = 0;
+    unsigned long long candidates = 0;   // query x entry pairs in adjacent cells
+};
+int build_query_side(const gj_index *h, const double *Q, int64_t nq, int qb, QuerySide *qs, cudaStream_t s);
+void free_query_side(QuerySide *qs, cudaStream_t s);
+
 // Autotuner (gj_tune.cu): runs the trials; *best_out (nullable) receives the
 // index of the pick, built, else it is freed.
 int autotune_impl(const double *points, int64_t n, int d, double eps, const gj_config *cfg, gj_tune_result *out,
@@ -178,10 +221,18 @@ struct gj_index {
     int64_t npad;
     int64_t G;
     int64_t nitems;
+    int64_t nadj;        // adjacency entries (sum of the cells' lists)
     int u;
     double e2, ew;
     int sms;
+    // the grid (for query sides of a similarity join)
+    int grid_k, grid_bits;
+    int grid_perm[gj::MAXK];
+    double grid_origin[gj::MAXK], grid_invw[gj::MAXK];
+    int64_t grid_nc[gj::MAXK], grid_stride[gj::MAXK];
+    int *perm_dev;       // device: REORDER permutation of all d dimensions
     int qb;              // query block size the items were built with
+    int q_align;         // > 0: items split at multiples of q_align positions
     int plain_ct;        // plain form: candidate tile, 0 = by d
     // tensor-core filter operands (GJ_TC_FILTER)
     bool tc_ready;

@@ -85,7 +85,7 @@ __device__ __forceinline__ int64_t upper_u(const double *__restrict__ U, int64_t
 // DIRECT = true: pairs go straight to the output through one global atomic
 // per warp (no staging, no commit/defer protocol); pairs past `cap` are
 // counted but not written.
-template <int CT, bool DIRECT = false>
+template <int CT, bool DIRECT = false, bool ASYM = false>
 __global__ void __launch_bounds__(JT) k_join_plain(JoinLaunch L)
 {
     constexpr int LOGCT = (CT == 64) ? 6 : (CT == 32 ? 5 : 4);
@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(JT) k_join_plain(JoinLaunch L)
                 H.cell = it.cell;
                 H.qbeg = it.qbeg;
                 H.qlen = it.qlen;
-                H.cell_end = L.ix.cell_start[it.cell + 1];
+                H.cell_end = ASYM ? 0 : L.ix.cell_start[it.cell + 1];
                 H.nb_begin = L.ix.adj_start[it.cell];
                 H.nb_end = L.ix.adj_start[it.cell + 1];
             }
@@ -148,18 +148,21 @@ __global__ void __launch_bounds__(JT) k_join_plain(JoinLaunch L)
         const uint32_t cell = H.cell, qbeg = H.qbeg, qlen = H.qlen;
         const int64_t nb_begin = H.nb_begin, nb_end = H.nb_end;
 
-        // ---- query block -> shared memory, Qs[j][qi]
+        // ---- query block -> shared memory, Qs[j][qi] (a similarity join's
+        // queries live in their own array)
+        const double *__restrict__ XQ = ASYM ? L.ix.XQ : X;
+        const int64_t qstride = ASYM ? L.ix.qnpad : npad;
         for (int idx = tid; idx < d * QB; idx += JT) {
             int j = idx / QB, qi = idx - j * QB;
-            Qs[idx] = (qi < (int)qlen) ? X[(int64_t)j * npad + qbeg + qi] : 0.0;
+            Qs[idx] = (qi < (int)qlen) ? XQ[(int64_t)j * qstride + qbeg + qi] : 0.0;
         }
 
         uint32_t tile_idx = 0, commit_tile = H.resume;
         const int u = L.ix.u;
         double ulo = 0.0, uhi = 0.0;
         if (u >= 0) {
-            ulo = X[(int64_t)u * npad + qbeg];
-            uhi = X[(int64_t)u * npad + qbeg + qlen - 1];
+            ulo = XQ[(int64_t)u * qstride + qbeg];
+            uhi = XQ[(int64_t)u * qstride + qbeg + qlen - 1];
         }
 
         for (int64_t nb0 = nb_begin; nb0 < nb_end && !H.stop; nb0 += NBCHUNK) {
@@ -168,7 +171,7 @@ __global__ void __launch_bounds__(JT) k_join_plain(JoinLaunch L)
             if (nb0 + tid < nb_end) {
                 uint32_t b = L.ix.adj[nb0 + tid];
                 int64_t cs, ce;
-                if (b == cell) {
+                if (!ASYM && b == cell) {
                     cs = qbeg;
                     ce = H.cell_end;
                 } else {
@@ -188,7 +191,7 @@ __global__ void __launch_bounds__(JT) k_join_plain(JoinLaunch L)
             const int nwin = (int)min((int64_t)NBCHUNK, nb_end - nb0);
             for (int w = 0; w < nwin && !H.stop; ++w) {
                 const int64_t ws = H.win_s[w], we = H.win_e[w];
-                const bool self = (H.win_b[w] == cell);
+                const bool self = !ASYM && (H.win_b[w] == cell);
                 for (int64_t t0 = ws; t0 < we; t0 += CT, ++tile_idx) {
                     if (tile_idx < commit_tile)
                         continue;   // committed by an earlier launch
@@ -263,7 +266,8 @@ __global__ void __launch_bounds__(JT) k_join_plain(JoinLaunch L)
                             if (em) {
                                 const uint32_t qpos = qbeg + qi;
                                 const uint32_t cpos = (uint32_t)(t0 + cj);
-                                const bool two = fin && (qpos != cpos);
+                                // both orientations, except a self-pair and a similarity join's (q, e)
+                                const bool two = fin && !ASYM && (qpos != cpos);
                                 unsigned em2 = __ballot_sync(FULL, two);
                                 if (count_only) {
                                     my_count += (fin ? 1 : 0) + (two ? 1 : 0);
@@ -274,7 +278,8 @@ __global__ void __launch_bounds__(JT) k_join_plain(JoinLaunch L)
                                         off = atomicAdd(&L.ctl->pos, (unsigned long long)cnt);
                                     off = __shfl_sync(FULL, off, 0);
                                     if (fin) {
-                                        const uint32_t a = L.ix.orig[qpos], b = L.ix.orig[cpos];
+                                        const uint32_t a = ASYM ? L.ix.qorig[qpos] : L.ix.orig[qpos];
+                                        const uint32_t b = L.ix.orig[cpos];
                                         const unsigned long long i1 = off + __popc(em & lt);
                                         if (i1 < L.cap)
                                             L.out[i1] = gj_pair{a, b};
@@ -294,7 +299,8 @@ __global__ void __launch_bounds__(JT) k_join_plain(JoinLaunch L)
                                         if (lane == 0)
                                             atomicOr(&L.ctl->err, kErrStaging);
                                     } else if (fin) {
-                                        uint32_t a = L.ix.orig[qpos], b = L.ix.orig[cpos];
+                                        uint32_t a = ASYM ? L.ix.qorig[qpos] : L.ix.orig[qpos];
+                                        uint32_t b = L.ix.orig[cpos];
                                         stg[off + __popc(em & lt)] = gj_pair{a, b};
                                         if (two)
                                             stg[off + __popc(em) + __popc(em2 & lt)] = gj_pair{b, a};
@@ -401,25 +407,25 @@ int plain_ctas_per_sm(int d, int ct_req)
 
 size_t plain_smem_bytes(int d, int ct) { return plain_smem(d, plain_ct(d, ct)); }
 
+template <int CT, bool ASYM>
+static cudaError_t launch_direct(const JoinLaunch &L, int grid, size_t sm, cudaStream_t s)
+{
+    cudaError_t e = cudaFuncSetAttribute(k_join_plain<CT, true, ASYM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sm);
+    if (e != cudaSuccess)
+        return e;
+    note_launch();
+    k_join_plain<CT, true, ASYM><<<grid, JT, sm, s>>>(L);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_join_plain_direct(const JoinLaunch &L, int grid, cudaStream_t s)
 {
     const int ct = plain_ct(L.ix.d, L.ix.ct);
     const size_t sm = plain_smem(L.ix.d, ct);
-    cudaError_t e;
-    if (ct == 64) {
-        e = cudaFuncSetAttribute(k_join_plain<64, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        if (e != cudaSuccess)
-            return e;
-        note_launch();
-        k_join_plain<64, true><<<grid, JT, sm, s>>>(L);
-    } else {
-        e = cudaFuncSetAttribute(k_join_plain<32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        if (e != cudaSuccess)
-            return e;
-        note_launch();
-        k_join_plain<32, true><<<grid, JT, sm, s>>>(L);
-    }
-    return cudaGetLastError();
+    if (L.ix.asym)
+        return ct == 64 ? launch_direct<64, true>(L, grid, sm, s) : launch_direct<32, true>(L, grid, sm, s);
+    return ct == 64 ? launch_direct<64, false>(L, grid, sm, s) : launch_direct<32, false>(L, grid, sm, s);
 }
 
 cudaError_t launch_join_plain(const JoinLaunch &L, int grid, cudaStream_t s)

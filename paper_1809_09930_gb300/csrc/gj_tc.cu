@@ -184,9 +184,11 @@ __device__ __noinline__ void tc_flush_survivors(const TcLaunch *__restrict__ T, 
     const int lane = threadIdx.x & 31;
     const double *__restrict__ X = T->J.ix.X;
     const int64_t npad = T->J.ix.npad;
-    const int d = T->J.ix.d;
     const TcJob *jp = T->jobs ? &T->jobs[job] : nullptr;
     const long long e2bits = __double_as_longlong(jp ? jp->e2 : T->J.ix.e2);
+    // a job's dimensions past its own d are zero in the combined layout and
+    // add exactly 0: the job's d suffices
+    const int d = jp ? jp->d : T->J.ix.d;
     for (uint32_t base = 0; base < n; base += 32) {
         const uint32_t i = base + lane;
         bool keep = false;
@@ -963,9 +965,9 @@ int tc_prepare(gj_index *h, const double *stats_host, const int *perm, cudaStrea
         c[j] = 0.5 * (stats_host[(size_t)perm[j] * 4 + 2] + stats_host[(size_t)perm[j] * 4 + 3]);
     double *centre = nullptr;
     unsigned long long *rmax = nullptr;
-    cudaError_t e = cudaMalloc(&centre, d * sizeof(double));
+    cudaError_t e = dev_alloc(&centre, d * sizeof(double), s);
     if (e == cudaSuccess)
-        e = cudaMalloc(&rmax, sizeof(unsigned long long));
+        e = dev_alloc(&rmax, sizeof(unsigned long long), s);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(centre, c.data(), d * sizeof(double), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess)
@@ -990,9 +992,9 @@ int tc_prepare(gj_index *h, const double *stats_host, const int *perm, cudaStrea
     const int64_t rows = h->npad + 512;
     const size_t bytes = (size_t)rows * Kp * 2;
     if (e == cudaSuccess)
-        e = cudaMalloc(&h->XA, bytes);
+        e = dev_alloc(&h->XA, bytes, s);
     if (e == cudaSuccess)
-        e = cudaMalloc(&h->XB, bytes);
+        e = dev_alloc(&h->XB, bytes, s);
     if (e == cudaSuccess)
         e = cudaMemsetAsync(h->XA, 0, bytes, s);
     if (e == cudaSuccess)
@@ -1003,10 +1005,8 @@ int tc_prepare(gj_index *h, const double *stats_host, const int *perm, cudaStrea
         k_tc_pack<<<(int)((n + 127) / 128), 128, 0, s>>>(h->X, n, h->npad, P, (uint4 *)h->XA, (uint4 *)h->XB);
         e = cudaGetLastError();
     }
-    if (e == cudaSuccess)
-        e = cudaStreamSynchronize(s);
     h->tc_centre = centre;   // kept: a many-jobs layout re-packs from it
-    cudaFree(rmax);
+    dev_free(rmax, s);
     if (e != cudaSuccess)
         return e == cudaErrorMemoryAllocation ? GJ_ERR_OOM : GJ_ERR_CUDA;
     const double Td = tc_threshold(h->info.eps, sigma, R0, d, Kp);

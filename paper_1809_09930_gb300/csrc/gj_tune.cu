@@ -286,11 +286,11 @@ int autotune_impl(const double *points, int64_t n, int d, double eps, const gj_c
             break;
         // tiles at the best k of this form
         const int dflt_ct = d <= 32 ? 64 : 32;
-        for (int qb : {120, 64}) {
+        for (int qb : {0, 64}) {   // 0: the default blocks (120 points plain; 128-aligned tensor-core)
             for (int ct : {64, 32}) {
                 if (tc && ct != 64)
                     continue;
-                if (qb == 120 && (tc || ct == dflt_ct))
+                if (qb == 0 && (tc || ct == dflt_ct))
                     continue;   // the default, timed in the sweep
                 Trial t;
                 t.cfg = base;
@@ -320,7 +320,7 @@ int autotune_impl(const double *points, int64_t n, int d, double eps, const gj_c
     }
     out->k = best_h->info.k;
     out->flags = best.cfg.flags;
-    out->query_block = best_h->qb;
+    out->query_block = best.cfg.query_block;   // 0 = the default blocks
     out->tile = best_h->tc_ready ? 0 : (best.cfg.tile ? best.cfg.tile : (d <= 32 ? 64 : 32));
     out->batch_pairs = bs;
     out->est_pairs = best.est_pairs;

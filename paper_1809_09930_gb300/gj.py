@@ -72,7 +72,8 @@ class gj_join_stats(C.Structure):
     _fields_ = [("pairs", C.c_uint64), ("launches", C.c_uint32), ("batches_planned", C.c_uint32),
                 ("batch_pairs", C.c_uint64), ("estimate", C.c_uint64), ("tc_survivors", C.c_uint64),
                 ("evaluated", C.c_uint64), ("dims", C.c_uint64), ("join_ms", C.c_double),
-                ("estimate_ms", C.c_double), ("total_ms", C.c_double), ("busy_ms", C.c_double)]
+                ("estimate_ms", C.c_double), ("total_ms", C.c_double), ("busy_ms", C.c_double),
+                ("candidates", C.c_uint64)]
 
 
 EXPORTS = ["gj_config_init", "gj_index_build", "gj_index_build_ex", "gj_self_join",
@@ -80,7 +81,7 @@ EXPORTS = ["gj_config_init", "gj_index_build", "gj_index_build_ex", "gj_self_joi
            "gj_last_status", "gj_status_string", "gj_version", "gj_probe_fp64_tflops",
            "gj_kernel_launches", "gj_debug_tc_tile", "gj_self_join_noalloc", "gj_batch_build",
            "gj_batch_self_join", "gj_batch_get_info", "gj_batch_free", "gj_autotune", "gj_batch_get_k",
-           "gj_neighbor_table"]
+           "gj_neighbor_table", "gj_join_qe"]
 
 _lib = None
 
@@ -136,6 +137,8 @@ def load(path: str | None = None):
     lib.gj_autotune.restype = C.c_int
     lib.gj_autotune.argtypes = [V, C.c_int64, C.c_int32, C.c_double, C.POINTER(gj_config),
                                 C.POINTER(gj_tune_result)]
+    lib.gj_join_qe.restype = C.c_int
+    lib.gj_join_qe.argtypes = [V, V, C.c_int64, V, C.c_uint64, C.POINTER(C.c_uint64)]
     lib.gj_neighbor_table.restype = C.c_int
     lib.gj_neighbor_table.argtypes = [V, V, V, C.c_uint64, C.POINTER(C.c_uint64)]
     lib.gj_batch_get_k.restype = C.c_int
@@ -239,6 +242,16 @@ def gj_self_join_part(h: int, part: int, nparts: int, out=None) -> tuple[int, in
     cnt = C.c_uint64(0)
     st = load().gj_self_join_part(h, int(part), int(nparts), p, cap, C.byref(cnt))
     del keep
+    return st, int(cnt.value)
+
+
+def gj_join_qe(h: int, queries, out=None) -> tuple[int, int]:
+    """Q join_eps E against the index h (over E); returns (status, count)."""
+    q, nq, d, keepq = _ptr_points(queries)
+    p, cap, keep = _ptr_pairs(out)
+    cnt = C.c_uint64(0)
+    st = load().gj_join_qe(h, q, nq, p, cap, C.byref(cnt))
+    del keep, keepq
     return st, int(cnt.value)
 
 
@@ -425,6 +438,17 @@ class Index:
         if st != GJ_OK:
             raise GJError(st, "gj_self_join (count)")
         return n
+
+    def join_qe(self, queries):
+        """The pairs (query row, entry row) within eps as a (m, 2) uint32 array."""
+        st, m = gj_join_qe(self.h, queries, None)
+        if st != GJ_OK:
+            raise GJError(st, "gj_join_qe (count)")
+        out = np.empty((max(m, 1), 2), dtype=np.uint32)
+        st, m2 = gj_join_qe(self.h, queries, out)
+        if st != GJ_OK:
+            raise GJError(st, "gj_join_qe")
+        return out[:m2]
 
     def neighbor_table(self):
         """(row_start, nbr) as CUDA tensors (int64 (n+1,), int32 (|R|,))."""

@@ -22,7 +22,7 @@ SRC = os.path.join(os.path.dirname(oracle.__file__), "gj_oracle.c")
 MUTANTS = {
     "drop_last_dim": ("    for (int j = 0; j < d; ++j) {\n        double t = a[j] - b[j];\n        s = s + t * t;\n    }\n    return s;\n}\n\n/* Same sum",
                       "    for (int j = 0; j < d - 1; ++j) {\n        double t = a[j] - b[j];\n        s = s + t * t;\n    }\n    return s;\n}\n\n/* Same sum"),
-    "strict_brute": ("a->d) <= a->e2)", "a->d) < a->e2)"),
+    "strict_brute": ("a->X + j * a->d, a->d) <= a->e2)", "a->X + j * a->d, a->d) < a->e2)"),
     "strict_grid": ("if (sd <= a->e2) {", "if (sd < a->e2) {"),
     "offsets_0_to_2": ("nb[j] = ci[j] + (r % 3) - 1;", "nb[j] = ci[j] + (r % 3);"),
     "reorder_ascending": ("while (b >= 0 && var[perm[b]] < var[p]) {", "while (b >= 0 && var[perm[b]] > var[p]) {"),
@@ -31,6 +31,9 @@ MUTANTS = {
                           "while (stop < e && a->Y[(size_t)a->order[stop] * d + a->u] - ui <= 0.0)"),
     "eps_not_squared": ("    double e2 = eps * eps;\n    brute_arg", "    double e2 = eps;\n    brute_arg"),
     "shortc_wrong_sign": ("        if (s > e2)\n            return s;", "        if (s < e2)\n            return s;"),
+    "qe_strict": ("a->E + j * a->d, a->d) <= a->e2)", "a->E + j * a->d, a->d) < a->e2)"),
+    "qe_swapped_orientation": ("kv_push(&a->out, ((uint64_t)i << 32) | (uint64_t)j);\n    return NULL;\n}\n\n/* Every pair",
+                               "kv_push(&a->out, ((uint64_t)j << 32) | (uint64_t)i);\n    return NULL;\n}\n\n/* Every pair"),
 }
 
 
@@ -71,6 +74,16 @@ def _pins_pass() -> bool:
         dif = Zi[:, None, :] - Zi[None, :, :]
         want = np.argwhere((dif * dif).sum(-1) <= 3.0).astype(np.uint32)
         if not np.array_equal(oracle.grid_join(Z, math.sqrt(3.0) * (1 + 1e-12), 2), want):
+            return False
+        # Q join E against an integer reference, and its orientation
+        Qz, Ez = synth.lattice(60, 4, seed=9, side=5), synth.lattice(90, 4, seed=10, side=5)
+        dq = Qz.astype(np.int64)[:, None, :] - Ez.astype(np.int64)[None, :, :]
+        wq = np.argwhere((dq * dq).sum(-1) <= 2).astype(np.uint32)
+        if not np.array_equal(oracle.brute_qe(Qz, Ez, math.sqrt(2.0)), wq):
+            return False
+        # the boundary itself: eps = 2 is exact, pairs at distance 2 belong to R
+        w4 = np.argwhere((dq * dq).sum(-1) <= 4).astype(np.uint32)
+        if not np.array_equal(oracle.brute_qe(Qz, Ez, 2.0), w4):
             return False
         return True
     except (MemoryError, ValueError):

@@ -265,3 +265,41 @@ def test_neighbor_table_empty_and_isolated_rows():
     row_start, nbr = oracle.neighbor_table(oracle.brute(X, 1.0), 4)
     assert list(row_start) == [0, 2, 3, 5, 6]
     assert list(nbr) == [0, 2, 1, 0, 2, 3]
+
+
+# ---------------------------------------------------------------------------
+# Q join_eps E (Sec. 3.1): the self-join is the case Q = E; on integer
+# coordinates every term is exact, so an integer reference decides each pair
+# ---------------------------------------------------------------------------
+
+def test_qe_with_q_equal_e_is_the_self_join():
+    X = synth.mixture(900, 7, 5)
+    assert np.array_equal(oracle.brute_qe(X, X, 0.2), oracle.brute(X, 0.2))
+
+
+@pytest.mark.parametrize("nq,ne,d,side,E2", [(150, 220, 4, 5, 2), (90, 400, 6, 4, 3), (1, 300, 3, 7, 5)])
+def test_qe_integer_reference(nq, ne, d, side, E2):
+    Q = synth.lattice(nq, d, seed=nq, side=side)
+    E = synth.lattice(ne, d, seed=ne + 1, side=side)
+    Qi, Ei = Q.astype(np.int64), E.astype(np.int64)
+    dif = Qi[:, None, :] - Ei[None, :, :]
+    want = np.argwhere((dif * dif).sum(-1) <= E2).astype(np.uint32)
+    got = oracle.brute_qe(Q, E, math.sqrt(E2) * (1 + 1e-12))
+    assert np.array_equal(got, want)
+
+
+def test_qe_boundary_is_inclusive():
+    Q = synth.lattice(120, 3, seed=31, side=5)
+    E = synth.lattice(160, 3, seed=32, side=5)
+    dif = Q.astype(np.int64)[:, None, :] - E.astype(np.int64)[None, :, :]
+    for eps, E2 in ((1.0, 1), (2.0, 4), (3.0, 9)):
+        want = np.argwhere((dif * dif).sum(-1) <= E2).astype(np.uint32)
+        assert np.array_equal(oracle.brute_qe(Q, E, eps), want)
+
+
+def test_qe_orientation_and_far_sets():
+    Q = np.array([[0.0], [5.0]])
+    E = np.array([[0.5], [10.0], [4.0]])
+    assert oracle.brute_qe(Q, E, 1.0).tolist() == [[0, 0], [1, 2]]
+    assert oracle.brute_qe(Q + 100.0, E, 1.0).size == 0
+    assert oracle.brute_qe(np.zeros((0, 1)), E, 1.0).size == 0
