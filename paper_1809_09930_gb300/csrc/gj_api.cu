@@ -156,6 +156,7 @@ IndexView view_of(const gj_index *h)
     v.e2 = h->e2;
     v.ew = h->ew;
     v.ct = h->plain_ct;
+    v.qb = h->qb;
     return v;
 }
 
@@ -212,7 +213,7 @@ int join_impl(gj_index *h, int part, int nparts, gj_pair *pairs_out, uint64_t ca
         h->last.total_ms = now_ms() - t_start;
         return GJ_OK;
     }
-    const int per_sm = h->tc_ready ? 1 : plain_ctas_per_sm(h->info.d, h->plain_ct);
+    const int per_sm = h->tc_ready ? 1 : plain_ctas_per_sm(h->info.d, h->plain_ct, h->qb);
     if (per_sm < 1)
         return GJ_ERR_UNSUPPORTED;
     const int grid = h->sms * per_sm;

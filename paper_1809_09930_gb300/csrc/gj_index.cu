@@ -807,6 +807,10 @@ int build_index(gj_index *h, const double *P, int64_t n, int d, double eps, int 
         // 128 positions, so that the 128-row A tile starts at the block itself
         h->q_align = (tc && h->cfg.query_block == 0) ? QB : 0;
         h->qb = h->q_align ? QB : (tc ? QB_TC : QB_PLAIN);
+        // plain form above 32 dimensions: blocks of 64, so the query tile
+        // (d x 64 doubles) leaves room for four CTAs per SM
+        if (!tc && d > 32 && h->cfg.query_block == 0)
+            h->qb = 64;
         if (h->cfg.query_block > 0)
             h->qb = std::min(h->cfg.query_block, tc ? QB_TC : QB);
         h->plain_ct = tc ? 0 : h->cfg.tile;

@@ -75,6 +75,7 @@ struct IndexView {
     double e2;      // fl(eps*eps)
     double ew;      // SORTIDU window half-width (eps widened)
     int ct;         // plain form: candidate tile (32 or 64), 0 = by d
+    int qb;         // most points of a work item (sizes the plain kernel's query tile)
     // similarity join Q join E (asym != 0): queries come from XQ/qorig, items and
     // adjacency are the query side's, candidates the entries'; one orientation
     int asym;
@@ -143,8 +144,8 @@ int build_index(gj_index *h, const double *P, int64_t n, int d, double eps, int 
 // ---- join kernels (gj_join.cu) -------------------------------------------
 cudaError_t launch_join_plain(const JoinLaunch &L, int grid, cudaStream_t s);
 cudaError_t launch_join_plain_direct(const JoinLaunch &L, int grid, cudaStream_t s);
-int plain_ctas_per_sm(int d, int ct = 0);
-size_t plain_smem_bytes(int d, int ct = 0);
+int plain_ctas_per_sm(int d, int ct, int qb);
+size_t plain_smem_bytes(int d, int ct, int qb);
 cudaError_t launch_fp64_probe(double *out, int iters, int grid, cudaStream_t s);
 
 // Per-job parameters of a many-jobs launch (gj_batch.cu).

@@ -85,7 +85,7 @@ __device__ __forceinline__ int64_t upper_u(const double *__restrict__ U, int64_t
 // DIRECT = true: pairs go straight to the output through one global atomic
 // per warp (no staging, no commit/defer protocol); pairs past `cap` are
 // counted but not written.
-template <int CT, bool DIRECT = false, bool ASYM = false>
+template <int CT, int QBT, bool DIRECT = false, bool ASYM = false>
 __global__ void __launch_bounds__(JT) k_join_plain(JoinLaunch L)
 {
     constexpr int LOGCT = (CT == 64) ? 6 : (CT == 32 ? 5 : 4);
@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(JT) k_join_plain(JoinLaunch L)
     SmemHdr &H = *reinterpret_cast<SmemHdr *>(smem_raw);
     const int d = L.ix.d;
     double *Qs = reinterpret_cast<double *>(smem_raw + ((sizeof(SmemHdr) + 15) & ~size_t(15)));
-    double *Cs = Qs + (size_t)d * QB;
+    double *Cs = Qs + (size_t)d * QBT;
 
     const int tid = threadIdx.x, lane = tid & 31;
     const unsigned lt = (1u << lane) - 1u;
@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(JT) k_join_plain(JoinLaunch L)
     const bool count_only = (L.out == nullptr);
     const bool staged = !count_only && !DIRECT;
     gj_pair *stg = staged ? L.staging + (size_t)blockIdx.x * L.stg_cap : nullptr;
-    const uint32_t flush_at = L.stg_cap > 2u * QB * CT ? L.stg_cap - 2u * QB * CT : 0u;
+    const uint32_t flush_at = L.stg_cap > 2u * QBT * CT ? L.stg_cap - 2u * QBT * CT : 0u;
 
     unsigned long long my_count = 0, my_dims = 0, my_pairs = 0;
 
@@ -152,8 +152,8 @@ __global__ void __launch_bounds__(JT) k_join_plain(JoinLaunch L)
         // queries live in their own array)
         const double *__restrict__ XQ = ASYM ? L.ix.XQ : X;
         const int64_t qstride = ASYM ? L.ix.qnpad : npad;
-        for (int idx = tid; idx < d * QB; idx += JT) {
-            int j = idx / QB, qi = idx - j * QB;
+        for (int idx = tid; idx < d * QBT; idx += JT) {
+            int j = idx / QBT, qi = idx - j * QBT;
             Qs[idx] = (qi < (int)qlen) ? XQ[(int64_t)j * qstride + qbeg + qi] : 0.0;
         }
 
@@ -249,7 +249,7 @@ __global__ void __launch_bounds__(JT) k_join_plain(JoinLaunch L)
                             }
                             bool fin = false;
                             if (act) {
-                                double t = Qs[j * QB + qi] - Cs[(j << LOGCT) + cj];
+                                double t = Qs[j * QBT + qi] - Cs[(j << LOGCT) + cj];
                                 s = __fma_rn(t, t, s);
                                 ++j;
                                 ++my_dims;
@@ -388,65 +388,62 @@ __global__ void __launch_bounds__(JT) k_join_plain(JoinLaunch L)
         atomicAdd(&L.ctl->busy, (unsigned long long)((long long)globaltimer_ns() - H.t_start));
 }
 
-static size_t plain_smem(int d, int ct)
+// Query tile rows held in shared memory: 64 when the work items hold at most
+// 64 points (a smaller footprint, more CTAs per SM at large d), else 128.
+static int plain_qbt(int qb) { return qb > 0 && qb <= 64 ? 64 : QB; }
+
+static size_t plain_smem(int d, int ct, int qbt)
 {
-    return ((sizeof(SmemHdr) + 15) & ~size_t(15)) + (size_t)d * (QB + ct) * sizeof(double);
+    return ((sizeof(SmemHdr) + 15) & ~size_t(15)) + (size_t)d * (qbt + ct) * sizeof(double);
 }
 
 static int plain_ct(int d, int ct = 0) { return ct == 32 || ct == 64 ? ct : (d <= 32 ? 64 : 32); }
 
-int plain_ctas_per_sm(int d, int ct_req)
+int plain_ctas_per_sm(int d, int ct_req, int qb)
 {
     int ct = plain_ct(d, ct_req);
-    size_t sm = plain_smem(d, ct);
+    size_t sm = plain_smem(d, ct, plain_qbt(qb));
     int per = (int)((227 * 1024) / (sm + 1024));
     if (per > 4)
         per = 4;
     return per < 1 ? 0 : per;
 }
 
-size_t plain_smem_bytes(int d, int ct) { return plain_smem(d, plain_ct(d, ct)); }
+size_t plain_smem_bytes(int d, int ct, int qb) { return plain_smem(d, plain_ct(d, ct), plain_qbt(qb)); }
 
-template <int CT, bool ASYM>
-static cudaError_t launch_direct(const JoinLaunch &L, int grid, size_t sm, cudaStream_t s)
+template <int CT, int QBT, bool DIRECT, bool ASYM>
+static cudaError_t launch_one(const JoinLaunch &L, int grid, size_t sm, cudaStream_t s)
 {
-    cudaError_t e = cudaFuncSetAttribute(k_join_plain<CT, true, ASYM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sm);
+    cudaError_t e = cudaFuncSetAttribute(k_join_plain<CT, QBT, DIRECT, ASYM>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess)
         return e;
     note_launch();
-    k_join_plain<CT, true, ASYM><<<grid, JT, sm, s>>>(L);
+    k_join_plain<CT, QBT, DIRECT, ASYM><<<grid, JT, sm, s>>>(L);
     return cudaGetLastError();
+}
+
+template <bool DIRECT, bool ASYM>
+static cudaError_t launch_by_shape(const JoinLaunch &L, int grid, cudaStream_t s)
+{
+    const int ct = plain_ct(L.ix.d, L.ix.ct);
+    const int qbt = plain_qbt(L.ix.qb);
+    const size_t sm = plain_smem(L.ix.d, ct, qbt);
+    if (ct == 64)
+        return qbt == 64 ? launch_one<64, 64, DIRECT, ASYM>(L, grid, sm, s)
+                         : launch_one<64, QB, DIRECT, ASYM>(L, grid, sm, s);
+    return qbt == 64 ? launch_one<32, 64, DIRECT, ASYM>(L, grid, sm, s)
+                     : launch_one<32, QB, DIRECT, ASYM>(L, grid, sm, s);
 }
 
 cudaError_t launch_join_plain_direct(const JoinLaunch &L, int grid, cudaStream_t s)
 {
-    const int ct = plain_ct(L.ix.d, L.ix.ct);
-    const size_t sm = plain_smem(L.ix.d, ct);
-    if (L.ix.asym)
-        return ct == 64 ? launch_direct<64, true>(L, grid, sm, s) : launch_direct<32, true>(L, grid, sm, s);
-    return ct == 64 ? launch_direct<64, false>(L, grid, sm, s) : launch_direct<32, false>(L, grid, sm, s);
+    return L.ix.asym ? launch_by_shape<true, true>(L, grid, s) : launch_by_shape<true, false>(L, grid, s);
 }
 
 cudaError_t launch_join_plain(const JoinLaunch &L, int grid, cudaStream_t s)
 {
-    const int ct = plain_ct(L.ix.d, L.ix.ct);
-    const size_t sm = plain_smem(L.ix.d, ct);
-    cudaError_t e;
-    if (ct == 64) {
-        e = cudaFuncSetAttribute(k_join_plain<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        if (e != cudaSuccess)
-            return e;
-        note_launch();
-        k_join_plain<64><<<grid, JT, sm, s>>>(L);
-    } else {
-        e = cudaFuncSetAttribute(k_join_plain<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        if (e != cudaSuccess)
-            return e;
-        note_launch();
-        k_join_plain<32><<<grid, JT, sm, s>>>(L);
-    }
-    return cudaGetLastError();
+    return launch_by_shape<false, false>(L, grid, s);
 }
 
 // ---------------------------------------------------------------------------

@@ -98,7 +98,7 @@ extern "C" int gj_self_join_noalloc(const gj_index *h, int32_t part, int32_t npa
         return st;
     if (nq == 0)
         return GJ_OK;
-    const int per_sm = plain_ctas_per_sm(h->info.d, h->plain_ct);
+    const int per_sm = plain_ctas_per_sm(h->info.d, h->plain_ct, h->qb);
     if (per_sm < 1)
         return GJ_ERR_UNSUPPORTED;
     cudaStream_t s = h->stream;
@@ -124,6 +124,7 @@ extern "C" int gj_self_join_noalloc(const gj_index *h, int32_t part, int32_t npa
     L.ix.npad = h->npad;
     L.ix.d = h->info.d;
     L.ix.ct = h->plain_ct;
+    L.ix.qb = h->qb;
     L.ix.u = h->u;
     L.ix.e2 = h->e2;
     L.ix.ew = h->ew;

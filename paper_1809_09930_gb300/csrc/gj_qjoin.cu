@@ -66,9 +66,15 @@ extern "C" int gj_join_qe(gj_index *h, const double *queries, int64_t nq, gj_pai
         return GJ_ERR_CUDA;
     cudaStream_t s = h->stream;
     const int d = h->info.d;
-    const int per_sm = plain_ctas_per_sm(d, h->plain_ct);
+    // query blocks small enough that every CTA of the persistent grid gets
+    // about eight (few queries against many entries would otherwise leave
+    // most of the grid idle behind a few long blocks); blocks of at most 64
+    // also shrink the kernel's query tile, which may fit more CTAs per SM
+    int per_sm = plain_ctas_per_sm(d, h->plain_ct, QB);
     if (per_sm < 1)
         return GJ_ERR_UNSUPPORTED;
+    const int qb = (int)std::max<int64_t>(32, std::min<int64_t>(QB_PLAIN, (nq / (8 * (int64_t)h->sms * per_sm)) & ~7));
+    per_sm = plain_ctas_per_sm(d, h->plain_ct, qb);
     const int grid = h->sms * per_sm;
 
     // queries on the device, finite
@@ -98,10 +104,7 @@ extern "C" int gj_join_qe(gj_index *h, const double *queries, int64_t nq, gj_pai
         return GJ_ERR_NONFINITE;
     }
 
-    // the query side; query blocks small enough that every CTA of the
-    // persistent grid gets about eight (few queries against many entries
-    // would otherwise leave most of the grid idle behind a few long blocks)
-    const int qb = (int)std::max<int64_t>(32, std::min<int64_t>(QB_PLAIN, (nq / (8 * (int64_t)grid)) & ~7));
+    // the query side
     QuerySide qs;
     int st = build_query_side(h, Q, nq, qb, &qs, s);
     cudaFree(Qd);
@@ -140,6 +143,7 @@ extern "C" int gj_join_qe(gj_index *h, const double *queries, int64_t nq, gj_pai
     L.ix.e2 = h->e2;
     L.ix.ew = h->ew;
     L.ix.ct = h->plain_ct;
+    L.ix.qb = qb;
     L.ix.asym = 1;
     L.ix.XQ = qs.XQ;
     L.ix.qorig = qs.qorig;

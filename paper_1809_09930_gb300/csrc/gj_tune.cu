@@ -55,7 +55,7 @@ constexpr int kMaxParts = 32;
 // kMaxParts); never so many that the part has fewer items than CTAs.
 int trial_parts(const gj_index *h, int np_req)
 {
-    const int per_sm = h->tc_ready ? 1 : std::max(1, plain_ctas_per_sm(h->info.d, h->plain_ct));
+    const int per_sm = h->tc_ready ? 1 : std::max(1, plain_ctas_per_sm(h->info.d, h->plain_ct, h->qb));
     const int64_t ctas = (int64_t)h->sms * per_sm;
     const int64_t cap = std::max<int64_t>(1, std::min<int64_t>(kMaxParts, h->nitems / (2 * ctas)));
     return (int)(np_req > 0 ? std::min<int64_t>(np_req, cap) : cap);
