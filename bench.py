@@ -197,8 +197,28 @@ def cpu_baseline(runs, budget_s=15.0):
         evals += st["candidates"]
         secs += dt
         parts.append(f"first {m} points of the d={r['d']} set")
+    # one core, on a small sample of the first set (the oracle's rate per core)
+    r = runs[0]
+    X1 = synth.generate(r["kind"], 6000, r["d"], r["seed"])
+    t = time.perf_counter()
+    st1 = oracle.grid_count(X1, r["eps"], k=1, nthreads=1)
+    one = st1["candidates"] / (time.perf_counter() - t)
     return {"value": evals / secs, "unit": "distance evals/s", "cores": cores, "kind": "oracle",
-            "sample": "; ".join(parts) + f"; {secs:.1f} s of CPU work"}
+            "sample": "; ".join(parts) + f"; {secs:.1f} s of CPU work",
+            "value_one_core": one, "one_core_sample": f"first 6000 points of the d={r['d']} set",
+            "cpu_model": _cpu_model()}
+
+
+def _cpu_model() -> str:
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part", "hardware")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
 
 
 def reference_arm(args, runs):
@@ -602,8 +622,12 @@ def main():
             pk = json.load(f)
         peak = pk.get("bf16_tflops_sustained") or pk.get("bf16_tflops")
         achieved = col["flops"] / join_s / 1e12
+        # DRAM traffic of one 2M-point d = 32 launch: the ncu capture of a 1M-point launch of this
+        # kernel (13.29 GB: B-tile re-reads served mostly from L2) scaled by its candidate pairs (x 4)
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None, "kernel": "k_join_tc",
+                "frac": achieved / peak, "traffic": 53.2e9 if args.workload == "paper" else None,
+                "traffic_note": "bytes per d=32 launch at n=2e6, scaled from a 1e6-point ncu capture",
+                "kernel": "k_join_tc",
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (fp16 runs at the bf16 rate)",
                 "survivors_per_step": col["survivors"] / steps}
 
