@@ -45,7 +45,9 @@ extern "C" {
 #define GJ_ERR_CUDA          -4  /* a CUDA runtime call or kernel launch failed                      */
 #define GJ_ERR_CAPACITY      -5  /* |R| > cap: *count holds |R|; output contents unspecified         */
 #define GJ_ERR_TIMEOUT       -6  /* a bounded device-side wait ran out; the context stays usable     */
-#define GJ_ERR_UNSUPPORTED   -7  /* no usable device (needs compute capability 10.3, sm_103a)        */
+#define GJ_ERR_UNSUPPORTED   -7  /* no usable device (needs compute capability 10.3, sm_103a), or a
+                                 * join whose tiles do not fit shared memory (plain form: d above
+                                 * about 290 with the default query block)                        */
 #define GJ_ERR_TOO_LARGE     -8  /* n >= 2^32 (pair ids are 32-bit) or d > GJ_MAX_DIMS               */
 
 #define GJ_MAX_DIMS 1024
@@ -128,7 +130,10 @@ void gj_config_init(gj_config *cfg);
  *           cudaPointerGetAttributes.  It is copied; the caller keeps ownership
  *           and may free or change it after the call returns.
  *   n       number of points, 0 <= n < 2^32.
- *   d       dimensions, 1 <= d <= GJ_MAX_DIMS.
+ *   d       dimensions, 1 <= d <= GJ_MAX_DIMS.  The plain join holds a query
+ *           tile and a candidate tile of d FP64 rows in shared memory: up to
+ *           about 290 dimensions with the default blocks (64 queries x 32
+ *           candidates above 32 dimensions); the tensor-core form up to 124.
  *   eps     search distance, finite and > 0.
  *   k       indexed dimensions: 0 = choose automatically (Sec. 4.1 trade-off),
  *           else 1 <= k <= min(d, 8).  The library may index fewer dimensions

@@ -22,9 +22,11 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <map>
 #include <mutex>
 #include <new>
+#include <thread>
 #include <vector>
 
 #include "gj_internal.cuh"
@@ -217,13 +219,67 @@ gj_batch *build_batch(const gj_job *jobs, int32_t njobs, const gj_config &cfg, c
     // layout, so blocks aligned within the job would not stay aligned
     jc.query_block = QB_TC;
     jc.tile = 0;
-    for (int32_t j = 0; j < njobs && st == GJ_OK; ++j) {
-        jc.k = ks[j];
-        hs[j] = gj_index_build_ex(jobs[j].points, jobs[j].n, jobs[j].d, jobs[j].eps, &jc);
-        if (!hs[j]) {
-            st = gj_last_status();
-            break;
+    // The jobs' indices are built by a few host threads, each on its own
+    // stream, largest jobs first: a build is a chain of short kernels and
+    // host round trips, so several chains overlap on the device.
+    {
+        std::vector<int32_t> by_size((size_t)njobs);
+        for (int32_t j = 0; j < njobs; ++j)
+            by_size[j] = j;
+        std::stable_sort(by_size.begin(), by_size.end(),
+                         [&](int32_t a, int32_t c) { return jobs[a].n > jobs[c].n; });
+        const int nthreads = (int)std::min<int32_t>(8, njobs);
+        std::vector<cudaStream_t> streams((size_t)nthreads, nullptr);
+        std::vector<int> tst((size_t)nthreads, GJ_OK);
+        std::atomic<int32_t> next{0};
+        for (int t = 0; t < nthreads && e == cudaSuccess; ++t)
+            e = cudaStreamCreateWithFlags(&streams[t], cudaStreamNonBlocking);
+        // the inputs may still be in flight on the caller's stream
+        cudaEvent_t ready = nullptr;
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ready, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(ready, s);
+        for (int t = 0; t < nthreads && e == cudaSuccess; ++t)
+            e = cudaStreamWaitEvent(streams[t], ready, 0);
+        st = cuda_status(e);
+        if (st == GJ_OK) {
+            std::vector<std::thread> pool;
+            for (int t = 0; t < nthreads; ++t) {
+                pool.emplace_back([&, t]() {
+                    cudaSetDevice(dev);
+                    gj_config tc = jc;
+                    tc.stream = (void *)streams[t];
+                    for (;;) {
+                        const int32_t i = next.fetch_add(1);
+                        if (i >= njobs || tst[t] != GJ_OK)
+                            break;
+                        const int32_t j = by_size[i];
+                        tc.k = ks[j];
+                        hs[j] = gj_index_build_ex(jobs[j].points, jobs[j].n, jobs[j].d, jobs[j].eps, &tc);
+                        if (!hs[j])
+                            tst[t] = gj_last_status();
+                    }
+                    if (cudaStreamSynchronize(streams[t]) != cudaSuccess && tst[t] == GJ_OK)
+                        tst[t] = GJ_ERR_CUDA;
+                });
+            }
+            for (auto &th : pool)
+                th.join();
+            for (int t = 0; t < nthreads; ++t)
+                if (tst[t] != GJ_OK)
+                    st = tst[t];
         }
+        // from here on every job's memory is used and released in the order of
+        // the batch's stream
+        for (int32_t j = 0; j < njobs; ++j)
+            if (hs[j])
+                hs[j]->stream = s;
+        if (ready)
+            cudaEventDestroy(ready);
+        for (auto sm : streams)
+            if (sm)
+                cudaStreamDestroy(sm);
+    }
+    for (int32_t j = 0; j < njobs && st == GJ_OK; ++j) {
         b->k_job.push_back(hs[j]->info.k);
         G_total += hs[j]->G;
         I_total += hs[j]->nitems;

@@ -652,28 +652,38 @@ __global__ void k_item_counts(const int64_t *__restrict__ cell_start, int64_t G,
 
 // items of cell c at [istart[c], ...); cost key = ~float bits of the load
 // estimate (ascending key = descending load); also sums candidate pairs.
+// One warp per cell, its lanes taking the cell's items in turn (a large
+// cell holds thousands of items).
 __global__ void k_items(const int64_t *__restrict__ cell_start, int64_t G, int qb, int align,
                         const int64_t *__restrict__ istart, const int64_t *__restrict__ nbsum,
                         Item *__restrict__ items, uint64_t *__restrict__ key, uint32_t *__restrict__ val,
                         unsigned long long *__restrict__ cand)
 {
-    int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int64_t c = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     if (c >= G)
         return;
     const int64_t s = cell_start[c], e = cell_start[c + 1], len = e - s;
     const int64_t nb = nbsum[c];
-    int64_t it = istart[c];
-    for (int64_t q = s; q < e; ++it) {
-        const int64_t qe = align > 0 ? min(e, (q / align + 1) * align) : min(e, q + qb);
+    const int64_t cnt = align > 0 ? (len > 0 ? (e - 1) / align - s / align + 1 : 0) : (len + qb - 1) / qb;
+    for (int64_t i = lane; i < cnt; i += 32) {
+        int64_t q, qe;
+        if (align > 0) {
+            q = i == 0 ? s : (s / align + i) * align;
+            qe = min(e, (s / align + i + 1) * align);
+        } else {
+            q = s + i * qb;
+            qe = min(e, q + qb);
+        }
+        const int64_t it = istart[c] + i;
         const uint32_t ql = (uint32_t)(qe - q);
         items[it] = Item{(uint32_t)c, (uint32_t)q, ql, 0u};
-        float load = (float)ql * (float)(nb + (e - q));
+        const float load = (float)ql * (float)(nb + (e - q));
         key[it] = (uint64_t)(~__float_as_uint(load));
         val[it] = (uint32_t)it;
-        q = qe;
     }
-    unsigned long long pairs = (unsigned long long)(len * (len - 1) / 2) + (unsigned long long)(len * nb);
-    atomicAdd(cand, pairs);
+    if (lane == 0)
+        atomicAdd(cand, (unsigned long long)(len * (len - 1) / 2) + (unsigned long long)(len * nb));
 }
 
 // Similarity join: query blocks of qb points per query cell; load = block
@@ -983,8 +993,8 @@ int build_index(gj_index *h, const double *P, int64_t n, int d, double eps, int 
                 goto done;
             }
             note_launch();
-            k_items<<<(int)grid_blocks(G, 256), 256, 0, s>>>(h->cell_start, G, h->qb, h->q_align, cnt, nbsum, h->items, k0, v0,
-                                                             cand_dev);
+            k_items<<<(int)grid_blocks(G * 32, 256), 256, 0, s>>>(h->cell_start, G, h->qb, h->q_align, cnt, nbsum,
+                                                                  h->items, k0, v0, cand_dev);
             GJ_TRY(cudaGetLastError());
             GJ_TRY(radix_sort_pairs(k0, v0, k1, v1, nitems, 0, 32, counts, counts_cap, s));
             GJ_TRY(cudaMemcpyAsync(h->order, v0, nitems * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));

@@ -212,3 +212,17 @@ def test_mixture_config_full(name):
     ref = oracle.grid_join(X, w["eps"], 6)
     got, _, _ = _join(X, w["eps"], k=0)
     assert_parity(X, w["eps"], got, ref)
+
+
+def test_wide_points_plain_and_the_shared_memory_limit():
+    """d = 200 joins in the plain form (query tile 64 x 200 doubles); far above
+    the shared-memory limit the join reports GJ_ERR_UNSUPPORTED instead of
+    launching."""
+    X = synth.generate("mixture", 1500, 200, seed=200)
+    eps = 1.2
+    got, _, _ = _join(X, eps, k=2)
+    assert_parity(X, eps, got, oracle.brute(X, eps))
+    W = synth.uniform(300, 400, 4)
+    with gj.Index(W, 0.5, k=1) as ix:
+        st, _ = gj.gj_self_join(ix.h, None)
+        assert st == gj.GJ_ERR_UNSUPPORTED
