@@ -487,11 +487,11 @@ def bench_qe(args):
 
 def main():
     args = parse()
-    if args.workload == "jobs" and args.impl == "ours":
-        bench_jobs(args)
-        return
-    if args.workload == "qe" and args.impl == "ours":
-        bench_qe(args)
+    if args.workload in ("jobs", "qe") and args.impl == "ours":
+        # one-GPU workloads: under torchrun rank 0 runs them, the other ranks exit
+        if int(os.environ.get("RANK", "0")) != 0:
+            return
+        (bench_jobs if args.workload == "jobs" else bench_qe)(args)
         return
     runs = workload(args)
     if args.impl == "reference":

@@ -88,3 +88,39 @@ def test_config_layout_matches_header(lib):
     from paper_1809_09930_gb300 import gj
     assert ctypes.sizeof(gj.gj_config) == 4 + 4 + 8 + 8 + 4 + 4 + 4 + 5 * 4   # 56, as before
     assert ctypes.sizeof(gj.gj_tune_result) == 4 * 4 + 8 * 4 + 4 * 2
+
+
+@pytest.mark.parametrize("n,d,eps,want", [
+    (1 << 32, 2, 0.5, "GJ_ERR_TOO_LARGE"),       # pair ids are 32-bit
+    (10, 1025, 0.5, "GJ_ERR_TOO_LARGE"),         # d > GJ_MAX_DIMS
+    (10, 0, 0.5, "GJ_ERR_INVALID_ARG"),
+    (-1, 4, 0.5, "GJ_ERR_INVALID_ARG"),
+    (10, 4, 0.0, "GJ_ERR_INVALID_ARG"),
+    (10, 4, float("nan"), "GJ_ERR_INVALID_ARG"),
+    (10, 4, float("inf"), "GJ_ERR_INVALID_ARG"),
+])
+def test_build_argument_ranges_rejected_on_the_host(lib, n, d, eps, want):
+    """Sizes and eps outside the contract fail before any device work (no GPU
+    needed); the points pointer is never read."""
+    import ctypes
+    from paper_1809_09930_gb300 import gj
+    dummy = (ctypes.c_double * 8)()
+    cfg = gj.gj_config_init()
+    h = lib.gj_index_build_ex(ctypes.cast(dummy, ctypes.c_void_p), n, d, eps, ctypes.byref(cfg))
+    assert not h
+    assert lib.gj_last_status() == getattr(gj, want)
+
+
+def test_null_handles_and_buffers_rejected(lib):
+    import ctypes
+    from paper_1809_09930_gb300 import gj
+    cnt = ctypes.c_uint64(0)
+    assert lib.gj_self_join(None, None, 0, ctypes.byref(cnt)) == gj.GJ_ERR_INVALID_ARG
+    assert lib.gj_join_qe(None, None, 0, None, 0, ctypes.byref(cnt)) == gj.GJ_ERR_INVALID_ARG
+    assert lib.gj_neighbor_table(None, None, None, 0, ctypes.byref(cnt)) == gj.GJ_ERR_INVALID_ARG
+    assert lib.gj_batch_self_join(None, None, None, None) == gj.GJ_ERR_INVALID_ARG
+    assert lib.gj_batch_build(None, 0, None) is None
+    assert lib.gj_last_status() == gj.GJ_ERR_INVALID_ARG
+    r = gj.gj_tune_result()
+    assert lib.gj_autotune(None, 10, 4, 0.5, None, ctypes.byref(r)) == gj.GJ_ERR_INVALID_ARG
+    lib.gj_batch_free(None)

@@ -150,3 +150,15 @@ def test_paper_syn16d2m_tc_sampled_queries():
         # the reverse orientation of every listed pair is present too
         rev = int(((out[:, 1] == q)).sum().item())
         assert rev == got.size
+
+
+def test_large_skewed_plain_equals_tc_count():
+    """The 5M x 18 skewed set in both forms: the plain FP64 join and the
+    tensor-core filtered join count the same |R|."""
+    w = _w("skewed")
+    X = torch.from_numpy(synth.skewed(w["n"], w["d"], w["seed"])).cuda()
+    with gj.Index(X, w["eps"], k=0) as ip:
+        n_plain = ip.count()
+    with gj.Index(X, w["eps"], k=0, flags=TC) as it:
+        n_tc = it.count()
+    assert n_plain == n_tc > 300_000_000
