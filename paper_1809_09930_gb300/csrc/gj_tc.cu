@@ -277,7 +277,7 @@ __device__ __forceinline__ uint32_t hit_mask32(const uint32_t (&v)[32], float Tf
 // valid survivors marked in each lane's hit mask (warp-aggregated), flushing
 // the queue through the FP64 recheck when it would overflow.  Returns the new
 // queue length.
-__device__ __noinline__ uint32_t tc_queue_bits(const TcLaunch *__restrict__ T, uint32_t mask, uint32_t col0,
+__device__ __forceinline__ uint32_t tc_queue_bits(const TcLaunch *__restrict__ T, uint32_t mask, uint32_t col0,
                                                uint32_t qpos, uint32_t r0,
                                                uint32_t *sq, uint32_t *sc, uint32_t nq, gj_pair *stg, uint32_t *cnt,
                                                uint32_t *flush_req, unsigned long long *surv_sh,
