@@ -291,7 +291,7 @@ def plain_sampled(gj, data, col, stream, peak, nparts=32):
     """The plain FP64 join of the d = 32 and 64 sets would take minutes, so it
     runs on one part of an entity partition (Sec. 6.2: load-ordered work items
     dealt round-robin, a load-stratified 1/nparts sample, count only); its
-    kernel busy time (each CTA's start-to-exit time averaged over the grid) x
+    kernel busy time (each SM's occupied span averaged over the SMs) x
     nparts estimates the whole join, beside the tensor-core form's measured
     join time of the same set."""
     res = {}
@@ -623,9 +623,9 @@ def main():
         peak = pk.get("bf16_tflops_sustained") or pk.get("bf16_tflops")
         achieved = col["flops"] / join_s / 1e12
         # DRAM traffic of one 2M-point d = 32 launch: the ncu capture of a 1M-point launch of this
-        # kernel (12.92 GB: B-tile re-reads served mostly from L2) scaled by its candidate pairs (x 4)
+        # kernel (9.45 GB: B-tile re-reads served mostly from L2) scaled by its candidate pairs (x 4)
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": 51.7e9 if args.workload == "paper" else None,
+                "frac": achieved / peak, "traffic": 37.8e9 if args.workload == "paper" else None,
                 "traffic_note": "bytes per d=32 launch at n=2e6, scaled from a 1e6-point ncu capture",
                 "kernel": "k_join_tc",
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (fp16 runs at the bf16 rate)",

@@ -59,6 +59,8 @@ extern "C" {
 #define GJ_TC_FILTER  (1u << 3)  /* tensor-core candidate filter + exact FP64 recheck (no paper counterpart) */
 #define GJ_AUTOTUNE   (1u << 4)  /* build: pick k, query block, tile and b_s by timed trials (gj_autotune) */
 #define GJ_TUNE_FORM  (1u << 5)  /* autotune: also try both forms (plain and GJ_TC_FILTER), keep the faster */
+#define GJ_HOST_BATCHED (1u << 6) /* host output always through the result batches of Sec. 3.2.2, even
+                                       where the device can address the host buffer directly */
 #define GJ_DEFAULT_FLAGS (GJ_REORDER | GJ_SORTIDU | GJ_SHORTC)
 
 /* One result pair: original row indices of the two points. */
@@ -113,9 +115,10 @@ typedef struct {
     double   join_ms;        /* device time of the join kernels (CUDA events)                   */
     double   estimate_ms;    /* device time of the sampled estimate                              */
     double   total_ms;       /* host wall time of the call                                       */
-    double   busy_ms;        /* join kernels: each CTA's start-to-exit time, averaged over the
-                              * CTAs of a launch, summed over launches (the join's work spread
-                              * evenly over the grid: its time without the tail)                  */
+    double   busy_ms;        /* join kernels: each SM's occupied span (earliest CTA start to
+                              * latest CTA exit), averaged over the SMs of a launch, summed over
+                              * launches (the join's work spread evenly over the SMs: its time
+                              * without the tail)                                                 */
     uint64_t candidates;     /* gj_join_qe: query x entry pairs in adjacent cells (its evals unit) */
 } gj_join_stats;
 
@@ -192,9 +195,12 @@ int gj_autotune(const double *points, int64_t n, int32_t d, double eps, const gj
  *   cap        capacity of pairs_out in pairs.
  *   count      out: |R| (always the full size, also on GJ_ERR_CAPACITY).
  * Returns GJ_OK, or GJ_ERR_CAPACITY when |R| > cap (the contents of pairs_out
- * are then unspecified), or another error code.  Host output is copied in
- * result batches on a second stream while the next batch runs; pinned host
- * memory lets those copies overlap the join.
+ * are then unspecified), or another error code.  Pageable host output is
+ * copied in result batches (Sec. 3.2.2) on a second stream while the next
+ * batch runs.  Pinned host memory that the device can address (cudaMallocHost,
+ * cudaHostAlloc, mapped cudaHostRegister; CUDA reports a device pointer for
+ * it) is written by the join kernels directly, in one pass as for device
+ * memory; GJ_HOST_BATCHED in the build flags sends it through the batches.
  */
 int gj_self_join(gj_index *h, gj_pair *pairs_out, uint64_t cap, uint64_t *count);
 
@@ -364,7 +370,10 @@ int gj_probe_fp64_tflops(int32_t device, double *tflops);
  * tensor cores through the operand layout, descriptors and TMEM path of the
  * GJ_TC_FILTER join.  A and B are row-major [128][Kp] fp16 bit patterns in host
  * memory, Kp a multiple of 16 in [16, 128]; D is row-major [128][128] fp32 in
- * host memory.  Runs on the current device; returns GJ_OK or an error code. */
+ * host memory.  The tile is read back with the join's reducing TMEM load
+ * (values and per-lane minimum of each 32 columns); a minimum that differs from
+ * the minimum of the values returned gives GJ_ERR_CUDA.  Runs on the current
+ * device; returns GJ_OK or an error code. */
 int gj_debug_tc_tile(const uint16_t *A, const uint16_t *B, int32_t Kp, float *D);
 
 /* Measurement helper (no paper counterpart): number of CUDA kernels this

@@ -45,6 +45,21 @@ void pool_keep(int device)
     cudaGetLastError();
     done.fetch_or((uint64_t)1 << device);
 }
+gj_pair *device_view(gj_pair *p, bool allow_host)
+{
+    if (!p)
+        return nullptr;
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged)
+        return p;
+    if (allow_host && a.type == cudaMemoryTypeHost && a.devicePointer)
+        return static_cast<gj_pair *>(a.devicePointer);
+    return nullptr;
+}
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 unsigned long long launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
 }  // namespace gj
@@ -106,6 +121,7 @@ struct JoinBuffers {
     gj_pair *staging = nullptr;
     gj_pair *dbuf[2] = {nullptr, nullptr};
     uint32_t *queue = nullptr, *qtmp = nullptr, *sample = nullptr;
+    unsigned long long *span = nullptr, *hspan = nullptr;   // per-SM spans (device, pinned host)
     cudaEvent_t ev_k0 = nullptr, ev_k1 = nullptr, ev_ctl = nullptr, ev_drained[2] = {nullptr, nullptr};
     ~JoinBuffers()
     {
@@ -120,6 +136,8 @@ struct JoinBuffers {
         cudaFree(queue);
         cudaFree(qtmp);
         cudaFree(sample);
+        cudaFree(span);
+        cudaFreeHost(hspan);
         if (ev_k0) cudaEventDestroy(ev_k0);
         if (ev_k1) cudaEventDestroy(ev_k1);
         if (ev_ctl) cudaEventDestroy(ev_ctl);
@@ -127,18 +145,6 @@ struct JoinBuffers {
             if (e) cudaEventDestroy(e);
     }
 };
-
-bool is_device_ptr(const void *p)
-{
-    if (!p)
-        return false;
-    cudaPointerAttributes a{};
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
 
 IndexView view_of(const gj_index *h)
 {
@@ -160,22 +166,48 @@ IndexView view_of(const gj_index *h)
     return v;
 }
 
-// One launch of the persistent join; reads back the control block.
+// Busy time of one launch: each SM's occupied span (earliest CTA start to
+// latest CTA exit) averaged over the SMs that ran CTAs, in ms.  Co-resident
+// CTAs that finish early leave their SM's span unchanged, so the figure never
+// credits the survivors' speed-up to the whole SM.
+double mean_sm_span_ms(const unsigned long long *span)
+{
+    double sum = 0.0;
+    int used = 0;
+    for (int i = 0; i < kSmSlots; ++i) {
+        const unsigned long long t1 = span[kSmSlots + i];
+        if (t1 == 0)
+            continue;
+        const unsigned long long t0 = ~span[i];
+        if (t1 > t0)
+            sum += (double)(t1 - t0);
+        ++used;
+    }
+    return used ? sum / used * 1e-6 : 0.0;
+}
+
+// One launch of the persistent join; reads back the control block and the
+// per-SM spans (their mean is added to *span_ms).
 int run_launch(gj_index *h, JoinBuffers &B, JoinLaunch L, int grid, JoinCtl init, JoinCtl *result,
-               double *kernel_ms)
+               double *kernel_ms, double *span_ms)
 {
     cudaStream_t s = h->stream;
     *B.hctl_up = init;
     cudaError_t e = cudaMemcpyAsync(B.ctl, B.hctl_up, sizeof(JoinCtl), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(B.span, 0, 2 * kSmSlots * sizeof(unsigned long long), s);
     if (e != cudaSuccess)
         return cuda_status(e);
     L.ctl = B.ctl;
+    L.sm_span = B.span;
     cudaEventRecord(B.ev_k0, s);
     e = h->tc_ready ? launch_join_tc(h, L, grid, s) : launch_join_plain(L, grid, s);
     if (e != cudaSuccess)
         return cuda_status(e);
     cudaEventRecord(B.ev_k1, s);
     e = cudaMemcpyAsync(B.hctl_dn, B.ctl, sizeof(JoinCtl), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(B.hspan, B.span, 2 * kSmSlots * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
     if (e != cudaSuccess)
         return cuda_status(e);
     cudaEventRecord(B.ev_ctl, s);
@@ -185,6 +217,7 @@ int run_launch(gj_index *h, JoinBuffers &B, JoinLaunch L, int grid, JoinCtl init
     float ms = 0.f;
     cudaEventElapsedTime(&ms, B.ev_k0, B.ev_k1);
     *kernel_ms += ms;
+    *span_ms += mean_sm_span_ms(B.hspan);
     *result = *B.hctl_dn;
     if (result->err & (kErrStaging | kErrDeferred)) {
         if (debug_on())
@@ -220,7 +253,10 @@ int join_impl(gj_index *h, int part, int nparts, gj_pair *pairs_out, uint64_t ca
     // pairs per CTA staging area: plain >= 4 tiles of output; tensor-core: two halves
     const uint32_t stg_cap = 1u << 16;
     const size_t stg_per_cta = h->tc_ready ? tc_staging_pairs_per_cta() : (size_t)stg_cap;
-    const bool dev_out = is_device_ptr(pairs_out);
+    // device memory, or pinned host memory the kernels can write directly
+    // (one pass, no result batches); pageable host memory goes through batches
+    gj_pair *const direct = device_view(pairs_out, !(h->cfg.flags & GJ_HOST_BATCHED));
+    const bool dev_out = direct != nullptr;
     const bool count_only_call = (cap == 0);
 
     JoinBuffers B;
@@ -233,6 +269,8 @@ int join_impl(gj_index *h, int part, int nparts, gj_pair *pairs_out, uint64_t ca
     TRYC(cudaMalloc(&B.ctl, sizeof(JoinCtl)));
     TRYC(cudaMallocHost(&B.hctl_up, sizeof(JoinCtl)));
     TRYC(cudaMallocHost(&B.hctl_dn, sizeof(JoinCtl)));
+    TRYC(cudaMalloc(&B.span, 2 * kSmSlots * sizeof(unsigned long long)));
+    TRYC(cudaMallocHost(&B.hspan, 2 * kSmSlots * sizeof(unsigned long long)));
     // a CTA defers at most the items in its pipeline when the output fills
     const uint32_t dcap = (uint32_t)grid * 8u;
     TRYC(cudaMalloc(&B.def[0], (size_t)dcap * sizeof(Deferred)));
@@ -280,8 +318,8 @@ int join_impl(gj_index *h, int part, int nparts, gj_pair *pairs_out, uint64_t ca
         JoinCtl init{};
         init.fail_base = ~0ull;
         JoinCtl res{};
-        double est_ms = 0.0;
-        int st0 = run_launch(h, B, Ls, grid, init, &res, &est_ms);
+        double est_ms = 0.0, est_span = 0.0;
+        int st0 = run_launch(h, B, Ls, grid, init, &res, &est_ms, &est_span);
         if (st0 != GJ_OK)
             return st0;
         estimate = (uint64_t)((double)res.counted * (double)nq / (double)ns);
@@ -344,7 +382,7 @@ int join_impl(gj_index *h, int part, int nparts, gj_pair *pairs_out, uint64_t ca
         gj_pair *lout = nullptr;
         if (!counting) {
             if (dev_out) {
-                lout = pairs_out + written;
+                lout = direct + written;
                 lcap = cap - written;
             } else {
                 lout = B.dbuf[launches & 1];
@@ -362,11 +400,10 @@ int join_impl(gj_index *h, int part, int nparts, gj_pair *pairs_out, uint64_t ca
         init.fail_base = ~0ull;
         init.head = head;
         JoinCtl res{};
-        st = run_launch(h, B, Lb, grid, init, &res, &kms);
+        st = run_launch(h, B, Lb, grid, init, &res, &kms, &busy_ms);
         if (st != GJ_OK)
             break;
         ++launches;
-        busy_ms += (double)res.busy / (double)grid * 1e-6;
         evaluated += res.evaluated;
         dims += res.dims;
         survivors += res.survivors;

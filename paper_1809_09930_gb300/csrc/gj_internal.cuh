@@ -48,7 +48,6 @@ struct JoinCtl {
     unsigned long long survivors;  // tensor-core filter survivors
     unsigned long long dims;       // dimensions evaluated (SHORTC depth summed over pairs)
     unsigned long long evaluated;  // candidate pairs evaluated
-    unsigned long long busy;       // ns from each CTA's start to its exit, summed over CTAs
     unsigned int head;             // main-queue dequeue counter (monotone across launches)
     unsigned int full;             // output filled during this launch
     unsigned int din_head;         // deferred-in dequeue counter
@@ -97,7 +96,27 @@ struct JoinLaunch {
     unsigned long long cap;
     gj_pair *staging;           // per-CTA staging areas
     uint32_t stg_cap;           // pairs per CTA
+    // optional (nullptr = not recorded): per SM slot (%smid mod kSmSlots), the
+    // complement of the earliest CTA start [0, kSmSlots) and the latest CTA
+    // exit [kSmSlots, 2 kSmSlots), in globaltimer ns; zero-initialised (the
+    // complement turns the minimum into a maximum, whose identity is zero)
+    unsigned long long *sm_span;
 };
+
+constexpr int kSmSlots = 256;
+
+#ifdef __CUDACC__
+// Record this CTA's start and exit in the launch's per-SM span slots.
+__device__ __forceinline__ void note_sm_span(unsigned long long *span, unsigned long long t0,
+                                             unsigned long long t1)
+{
+    uint32_t sm;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(sm));
+    sm %= (uint32_t)kSmSlots;
+    atomicMax(&span[sm], ~t0);
+    atomicMax(&span[kSmSlots + sm], t1);
+}
+#endif
 
 // Index memory comes from the device's stream-ordered pool: an allocation or
 // a free is queued on the build's stream and does not wait for the device
@@ -115,6 +134,10 @@ inline void dev_free(void *p, cudaStream_t s)
         cudaFreeAsync(p, s);
 }
 void pool_keep(int device);
+// A device-addressable view of an output buffer: device or managed memory as
+// it is; pinned host memory through the device pointer CUDA reports for it
+// (when allow_host); nullptr for pageable host memory.
+gj_pair *device_view(gj_pair *p, bool allow_host);
 
 // Count of kernels this library has launched (process-wide); read through
 // gj_kernel_launches().

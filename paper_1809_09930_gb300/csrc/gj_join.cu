@@ -384,8 +384,8 @@ __global__ void __launch_bounds__(JT) k_join_plain(JoinLaunch L)
         atomicAdd(&L.ctl->dims, my_dims);
         atomicAdd(&L.ctl->evaluated, my_pairs);
     }
-    if (tid == 0)
-        atomicAdd(&L.ctl->busy, (unsigned long long)((long long)globaltimer_ns() - H.t_start));
+    if (tid == 0 && L.sm_span)
+        note_sm_span(L.sm_span, (unsigned long long)H.t_start, globaltimer_ns());
 }
 
 // Query tile rows held in shared memory: 64 when the work items hold at most

@@ -9,8 +9,9 @@
 // gets the list of all adjacent non-empty entry cells (no symmetry to exploit),
 // and the plain FP64 SHORTC kernel runs in its asymmetric mode: queries from
 // the query array, candidates from the entries, one orientation (q, e) per
-// pair.  One launch writes the pairs straight into device memory (the
-// caller's, or a buffer of cap pairs for host output) with warp-aggregated
+// pair.  One launch writes the pairs straight into the caller's buffer when
+// the device can address it (device memory, pinned host memory), else into a
+// device buffer of cap pairs that is then copied to the host, with warp-aggregated
 // atomics and counts every pair, so a result larger than cap is reported with
 // its size.
 #include <cuda_runtime.h>
@@ -120,7 +121,8 @@ extern "C" int gj_join_qe(gj_index *h, const double *queries, int64_t nq, gj_pai
     uint32_t *queue = nullptr;
     gj_pair *dbuf = nullptr;
     JoinCtl hctl{};
-    const bool dev_out = pairs_out && device_memory(pairs_out);
+    gj_pair *const direct = device_view(pairs_out, !(h->cfg.flags & GJ_HOST_BATCHED));
+    const bool dev_out = direct != nullptr;
     uint64_t total = 0;
     e = cudaMalloc(&ctl, sizeof(JoinCtl));
     if (e == cudaSuccess) e = cudaMalloc(&queue, qs.nitems * sizeof(uint32_t));
@@ -161,7 +163,7 @@ extern "C" int gj_join_qe(gj_index *h, const double *queries, int64_t nq, gj_pai
     gj_pair *out = nullptr;
     if (e == cudaSuccess && cap > 0) {
         if (dev_out) {
-            out = pairs_out;
+            out = direct;
         } else {
             e = cudaMalloc(&dbuf, cap * sizeof(gj_pair));
             out = dbuf;

@@ -26,9 +26,10 @@
 //   warp 1   one thread issues tcgen05.mma (one M=128 x N=256 MMA per K step)
 //            into a double-buffered TMEM accumulator (2 x 256 fp32 columns)
 //            and commits to mbarriers;
-//   warps 2-9 epilogue: read the accumulators with tcgen05.ld, reduce each
-//            32-column chunk with three-input fp32 minima, mark the values
-//            <= T in per-lane bit masks, release the accumulator, then queue
+//   warps 2-9 epilogue: read the accumulators 32 columns at a time with
+//            tcgen05.ld.red, which also returns each lane's minimum, mark the
+//            values <= T of a chunk whose minimum is <= T in per-lane bit
+//            masks, release the accumulator, then queue
 //            the marked candidates and recheck them in FP64 in batches; exact
 //            pairs go to a double-buffered per-CTA staging area committed to
 //            the output per item (same resume protocol as the plain kernel).
@@ -248,21 +249,6 @@ __device__ __noinline__ void tc_flush_survivors(const TcLaunch *__restrict__ T, 
     }
 }
 
-// Minimum of 32 fp32 values as a tree of three-input minima: 16 operations,
-// dependency depth 4.
-__device__ __forceinline__ float min32_tree(const uint32_t (&v)[32])
-{
-    float t[11];
-#pragma unroll
-    for (int i = 0; i < 10; ++i)
-        t[i] = fmin3(__uint_as_float(v[3 * i]), __uint_as_float(v[3 * i + 1]), __uint_as_float(v[3 * i + 2]));
-    t[10] = fminf(__uint_as_float(v[30]), __uint_as_float(v[31]));
-    const float u0 = fmin3(t[0], t[1], t[2]);
-    const float u1 = fmin3(t[3], t[4], t[5]);
-    const float u2 = fmin3(t[6], t[7], t[8]);
-    return fmin3(fmin3(u0, u1, u2), t[9], t[10]);
-}
-
 // Bit i of the result: v[i] <= T (this lane's row against column i of a chunk).
 __device__ __forceinline__ uint32_t hit_mask32(const uint32_t (&v)[32], float Tf)
 {
@@ -368,6 +354,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
         // ------------------------------------------------------------ producer
         uint32_t seq = 0, nitem = 0;
         bool dead = false;
+        unsigned long long slots = 0;   // candidate pairs of the pushed tiles (lane 0)
         auto push = [&](const TileDesc &D, bool tile) -> bool {   // lane 0 only
             const uint32_t stage = seq % (uint32_t)NS;
             if (!mbar_wait(&S.empty_b[stage], ((seq / NS) & 1u) ^ 1u, abort, TC_LIMIT_NS))
@@ -455,9 +442,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
                                     dead = true;
                             }
                             pend = TileDesc{item, tile_idx, 0u, 0u, it.qbeg, it.qlen, qa, cr0, job, jtb, 0u, 0u};
+                            uint32_t nv = 0;
 #pragma unroll
-                            for (int w = 0; w < 8; ++w)
+                            for (int w = 0; w < 8; ++w) {
                                 pend.mask[w] = S.cmask[w];
+                                nv += __popc(S.cmask[w]);
+                            }
+                            slots += (unsigned long long)it.qlen * nv;
                             have = true;
                         }
                     }
@@ -543,6 +534,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
                 S.abort = 1;
                 atomicOr(&L.ctl->err, kErrTimeout);
             }
+            if (slots)
+                atomicAdd(&L.ctl->evaluated, slots);
         }
         __syncwarp();
     } else if (warp == 1) {
@@ -620,7 +613,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
         const int etid = threadIdx.x - 64;
         uint32_t turn = 0, es = 0, commit_tile = 0;
         bool failed = false, dead = false;
-        unsigned long long slots = 0;
         uint32_t *const sq = S.sq[e], *const sc = S.sc[e];
         uint32_t nq = 0;
         // tuning launches: the cycles from one item end to the next are the
@@ -661,55 +653,47 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
             }
             const bool is_tile = !(D.flags & (F_MARKER | F_TERM));
             const float Tf = T.jobs ? __uint_as_float(D.p3) : Tf0;
-            const uint32_t half = S.half;
-            gj_pair *stg = stg0 ? stg0 + (size_t)half * TC_STG : nullptr;
             uint32_t hm0 = 0, hm1 = 0, hm2 = 0, hm3 = 0;   // per-lane hit masks of the 4 chunks
             bool anyhit = false;
             uint32_t qpos = 0;
             if (is_tile && !failed) {
-                // valid rows of this thread's 128 columns, read before the
-                // accumulator (and with it the descriptor slot) is released
+                // valid rows of this thread's 128 columns: read only for a chunk
+                // with hits, before the accumulator (and with it the descriptor
+                // slot) is released
                 const uint32_t *vmp = S.tdesc[acc].mask + hh * 4;
-                const uint32_t vm0 = vmp[0], vm1 = vmp[1], vm2 = vmp[2], vm3 = vmp[3];
                 const uint32_t row = (uint32_t)(q * 32 + lane);
                 qpos = D.qa + row;
                 const bool rvalid = qpos >= D.qbeg && qpos < D.qbeg + D.qlen;
                 const uint32_t tb = tmem + ((uint32_t)(q * 32) << 16) + acc * 256u + (uint32_t)hh * 128u;
                 {
                     uint32_t va[32], vb[32];
-                    tmem_ld32(tb, va);
-                    tmem_ld32(tb + 32u, vb);
+                    float ma, mb;
+                    tmem_ld32_min(tb, va, ma);
+                    tmem_ld32_min(tb + 32u, vb, mb);
                     tmem_wait_ld();
-                    const float ma = min32_tree(va), mb = min32_tree(vb);
                     const bool ha = rvalid && ma <= Tf, hb = rvalid && mb <= Tf;
                     if (__any_sync(0xffffffffu, ha || hb)) {
                         anyhit = true;
                         if (ha)
-                            hm0 = hit_mask32(va, Tf) & vm0;
+                            hm0 = hit_mask32(va, Tf) & vmp[0];
                         if (hb)
-                            hm1 = hit_mask32(vb, Tf) & vm1;
+                            hm1 = hit_mask32(vb, Tf) & vmp[1];
                     }
                 }
                 {
                     uint32_t va[32], vb[32];
-                    tmem_ld32(tb + 64u, va);
-                    tmem_ld32(tb + 96u, vb);
+                    float ma, mb;
+                    tmem_ld32_min(tb + 64u, va, ma);
+                    tmem_ld32_min(tb + 96u, vb, mb);
                     tmem_wait_ld();
-                    const float ma = min32_tree(va), mb = min32_tree(vb);
                     const bool ha = rvalid && ma <= Tf, hb = rvalid && mb <= Tf;
                     if (__any_sync(0xffffffffu, ha || hb)) {
                         anyhit = true;
                         if (ha)
-                            hm2 = hit_mask32(va, Tf) & vm2;
+                            hm2 = hit_mask32(va, Tf) & vmp[2];
                         if (hb)
-                            hm3 = hit_mask32(vb, Tf) & vm3;
+                            hm3 = hit_mask32(vb, Tf) & vmp[3];
                     }
-                }
-                if (etid == 0) {
-                    const uint32_t *m = S.tdesc[acc].mask;
-                    const uint32_t nv = __popc(m[0]) + __popc(m[1]) + __popc(m[2]) + __popc(m[3]) + __popc(m[4]) +
-                                        __popc(m[5]) + __popc(m[6]) + __popc(m[7]);
-                    slots += (unsigned long long)D.qlen * nv;
                 }
             }
             // A warp with few hits queues them after releasing the accumulator.
@@ -727,6 +711,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
                 if (lane == 0)
                     mbar_arrive(&S.tmem_empty[acc]);
             }
+            const uint32_t half = S.half;
+            gj_pair *stg = stg0 ? stg0 + (size_t)half * TC_STG : nullptr;
             if (anyhit) {
                 const uint32_t cb = (uint32_t)hh * 128u;
                 if (__any_sync(0xffffffffu, hm0 != 0u))
@@ -835,8 +821,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
             S.abort = 1;
             atomicOr(&L.ctl->err, kErrTimeout);
         }
-        if (etid == 0 && slots)
-            atomicAdd(&L.ctl->evaluated, slots);
+
     }
 
     __syncthreads();
@@ -845,7 +830,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
             atomicAdd(&L.ctl->survivors, S.surv);
         if (S.counted)
             atomicAdd(&L.ctl->counted, S.counted);
-        atomicAdd(&L.ctl->busy, (unsigned long long)((long long)globaltimer() - S.t_start));
+        if (L.sm_span)
+            note_sm_span(L.sm_span, (unsigned long long)S.t_start, globaltimer());
     }
     if (S.abort) {
         // let copies and MMAs already issued land before the memory goes away
@@ -1167,11 +1153,19 @@ __global__ void k_tc_debug(const unsigned char *__restrict__ A, const unsigned c
             tc_fence_after();
             const int row = warp * 32 + lane;
             for (int c = 0; c < 4; ++c) {
+                // the join's load: the 32 values of this lane's row and their
+                // minimum, which must equal the minimum of the values returned
                 uint32_t v[32];
-                tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + c * 32u, v);
+                float mn;
+                tmem_ld32_min(tmem + ((uint32_t)(warp * 32) << 16) + c * 32u, v, mn);
                 tmem_wait_ld();
-                for (int i = 0; i < 32; ++i)
+                float m = __uint_as_float(v[0]);
+                for (int i = 0; i < 32; ++i) {
+                    m = fminf(m, __uint_as_float(v[i]));
                     D[row * 128 + c * 32 + i] = __uint_as_float(v[i]);
+                }
+                if (m != mn)
+                    atomicOr(err, 2u);
             }
         } else {
             atomicOr(err, 1u);
@@ -1240,6 +1234,8 @@ extern "C" int gj_debug_tc_tile(const uint16_t *A, const uint16_t *B, int32_t Kp
     cudaFree(dD);
     cudaFree(derr);
     if (e != cudaSuccess)
+        return GJ_ERR_CUDA;
+    if (herr & 2u)
         return GJ_ERR_CUDA;
     return herr ? GJ_ERR_TIMEOUT : GJ_OK;
 }

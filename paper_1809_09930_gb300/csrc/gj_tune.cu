@@ -8,11 +8,11 @@
 //     synchronous) and runs a count-only join over one part of an entity
 //     partition of the load-ordered work items (Sec. 6.2: block r goes to part
 //     r mod N_b, so a part is a load-stratified sample).  The part's join time
-//     is the kernel's busy time -- each CTA's start-to-exit time averaged over
-//     the grid, i.e. the part's work spread evenly, without the tail a small
-//     sample has -- scaled by N_b.  N_b comes from a first, finely sampled
-//     trial of the builder's own choice, so that a trial's join takes about
-//     40 ms (at most 32 parts);
+//     is the kernel's busy time -- each SM's occupied span (earliest CTA start
+//     to latest CTA exit) averaged over the SMs, i.e. the part's work spread
+//     evenly, without the tail a small sample has -- scaled by N_b.  N_b comes
+//     from a first, finely sampled trial of the builder's own choice, so that
+//     a trial's join takes about 40 ms (at most 32 parts);
 //   * k sweeps 1..min(d, 8) (1..3 for the tensor-core form) with the default
 //     tiles and stops once the cost has grown past twice the best for two
 //     consecutive k; then the tiles are tried at the best k;

@@ -34,6 +34,7 @@ GJ_SHORTC = 1 << 2
 GJ_TC_FILTER = 1 << 3
 GJ_AUTOTUNE = 1 << 4
 GJ_TUNE_FORM = 1 << 5
+GJ_HOST_BATCHED = 1 << 6
 GJ_DEFAULT_FLAGS = GJ_REORDER | GJ_SORTIDU | GJ_SHORTC
 
 

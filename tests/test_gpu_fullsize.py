@@ -106,11 +106,12 @@ def test_mixture_d90(flags):
 def test_large_skewed_streamed_to_pinned_host():
     """5M x 18 skewed set: the result (~3e8 pairs) is emitted in result batches
     (b_s = 1e8 when the estimate exceeds 3e8, Sec. 3.2.2) and streamed to
-    pinned host memory while the next batch runs."""
+    pinned host memory while the next batch runs (GJ_HOST_BATCHED: without it
+    the kernels would write the pinned buffer directly)."""
     w = _w("skewed")
     X = synth.skewed(w["n"], w["d"], w["seed"])
     Xd = torch.from_numpy(X).cuda()
-    with gj.Index(Xd, w["eps"], k=0, flags=TC) as ix:
+    with gj.Index(Xd, w["eps"], k=0, flags=TC | gj.GJ_HOST_BATCHED) as ix:
         n = ix.count()
         host = torch.empty((n, 2), dtype=torch.int32).pin_memory()
         st, m = gj.gj_self_join(ix.h, host)

@@ -155,6 +155,35 @@ def test_device_output_buffer():
     assert_parity(X, 0.85, got, ref)
 
 
+@pytest.mark.parametrize("form", ["plain", "tc"])
+def test_pinned_host_output_direct_and_batched(form):
+    """Pinned host memory that the device can address is written by the join
+    kernels in one pass, as device memory is; GJ_HOST_BATCHED sends it through
+    the result batches of Sec. 3.2.2 instead.  Both give R, neither writes past
+    |R|, and a buffer that is too small gives GJ_ERR_CAPACITY with |R|."""
+    torch = pytest.importorskip("torch")
+    X = synth.mixture(6000, 18, 6)
+    ref = oracle.brute(X, 0.35)
+    base = gj.GJ_DEFAULT_FLAGS | (gj.GJ_TC_FILTER if form == "tc" else 0)
+    for flags, one_pass in ((base, True), (base | gj.GJ_HOST_BATCHED, False)):
+        with gj.Index(X, 0.35, k=4, flags=flags, batch_pairs=70_000) as ix:
+            n = ix.count()
+            assert n == len(ref)
+            host = torch.full((n + 8, 2), -1, dtype=torch.int32).pin_memory()
+            st, m = gj.gj_self_join(ix.h, host)
+            stats = ix.stats()
+            assert st == gj.GJ_OK and m == n
+            if one_pass:
+                assert stats["launches"] == 1 and stats["batch_pairs"] == 0
+            else:
+                assert stats["launches"] > 3 and stats["batch_pairs"] == 70_000
+            assert int(host[n:].min()) == -1
+            assert_parity(X, 0.35, host[:n].numpy().view(np.uint32), ref)
+            small = torch.empty((n // 3, 2), dtype=torch.int32).pin_memory()
+            st, m2 = gj.gj_self_join(ix.h, small)
+            assert st == gj.GJ_ERR_CAPACITY and m2 == n
+
+
 def test_device_input_points():
     torch = pytest.importorskip("torch")
     X = synth.skewed(4000, 18, 8)

@@ -100,3 +100,19 @@ def test_qe_device_buffers_capacity_and_errors():
         assert st == gj.GJ_ERR_NONFINITE
         st, m0 = gj.gj_join_qe(ix.h, np.zeros((0, 8)), None)
         assert st == gj.GJ_OK and m0 == 0
+
+
+def test_qe_pinned_host_output_is_written_directly():
+    E = synth.uniform(3000, 8, 5)
+    Q = synth.uniform(2000, 8, 6)
+    with gj.Index(E, 0.3, k=2) as ix:
+        st, m = gj.gj_join_qe(ix.h, Q, None)
+        assert st == gj.GJ_OK and m > 0
+        host = torch.full((m + 4, 2), -1, dtype=torch.int32).pin_memory()
+        st, m2 = gj.gj_join_qe(ix.h, Q, host)
+        assert st == gj.GJ_OK and m2 == m
+        assert int(host[m:].min()) == -1
+        _assert_qe_parity(Q, E, 0.3, host[:m].numpy().view(np.uint32))
+        small = torch.empty((m - 1, 2), dtype=torch.int32).pin_memory()
+        st, m3 = gj.gj_join_qe(ix.h, Q, small)
+        assert st == gj.GJ_ERR_CAPACITY and m3 == m
