@@ -19,10 +19,13 @@
 // truncating adder's bound).  Every pair of R therefore survives.
 //
 // Kernel (one persistent CTA per SM, 320 threads):
-//   warp 0   producer: takes work items (query blocks of <= 120 points), loads
-//            the item's 128-row A tile and each 256-row candidate tile with
-//            bulk asynchronous copies (TMA) into a ring of shared-memory
-//            stages, and passes tile descriptors down a ring;
+//   warp 0   producer: takes work items (query blocks of <= 120 points),
+//            computes the SORTIDU windows of the adjacent cells (one per lane),
+//            packs them into 256-row candidate tiles under a valid-row mask
+//            (lane 0 alone, state in registers; whole tiles of a long window
+//            take a short path), loads the item's 128-row A tile and each
+//            candidate tile with bulk asynchronous copies (TMA) into a ring of
+//            shared-memory stages, and passes tile descriptors down a ring;
 //   warp 1   one thread issues tcgen05.mma (one M=128 x N=256 MMA per K step)
 //            into a double-buffered TMEM accumulator (2 x 256 fp32 columns)
 //            and commits to mbarriers;
@@ -93,7 +96,7 @@ struct TcShared {
     unsigned long long counted;  // pairs counted (count-only launches)
     long long t_item;            // tuning launches: clock of the last item end
     long long t_start;           // clock at the CTA's start
-    uint32_t cmask[8];           // producer: valid rows of the tile being packed
+    long long win[32][2];        // producer: one batch of SORTIDU windows [start, end)
 };
 
 struct TcLaunch {
@@ -109,16 +112,6 @@ struct TcLaunch {
     uint32_t a_bytes, b_bytes;
     uint32_t off_b, off_s;
 };
-
-// Set bits [lo, hi) of a 256-bit row mask (0 <= lo < hi <= 256).
-__device__ __forceinline__ void tc_set_rows(uint32_t *m, uint32_t lo, uint32_t hi)
-{
-    for (uint32_t w = lo >> 5; w <= ((hi - 1u) >> 5); ++w) {
-        const uint32_t a = max(lo, w * 32u) - w * 32u, b = min(hi, w * 32u + 32u) - w * 32u;
-        const uint32_t top = b >= 32u ? 0xffffffffu : ((1u << b) - 1u);
-        m[w] |= top & ~((1u << a) - 1u);
-    }
-}
 
 __device__ __forceinline__ int64_t tc_lower_u(const double *__restrict__ U, int64_t lo, int64_t hi, double ref,
                                               double ew)
@@ -416,48 +409,91 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
                 ulo = L.ix.X[(int64_t)u * L.ix.npad + it.qbeg];
                 uhi = L.ix.X[(int64_t)u * L.ix.npad + it.qbeg + it.qlen - 1];
             }
+            // Tile packing runs in lane 0 alone: the open tile [cr0, cr0 + TC_N),
+            // its valid-row mask cm, the tile waiting to be pushed (pend) and
+            // the flags live in lane 0's registers; the other lanes only compute
+            // the windows and take part in the broadcasts once per batch.
             uint32_t tile_idx = 0;
             bool have = false, first = true, trunc = false;
             TileDesc pend{};
-            // the tile being packed: rows [cr0, cr0 + TC_N); its valid-row mask
-            // lives in shared memory (lane 0); every other value is warp-uniform
             bool open = false;
             uint32_t cr0 = 0;
-            auto close_tile = [&]() {
+            uint32_t cm[8];
+            auto close_tile = [&](bool full) {   // lane 0 only
                 if (!open)
                     return;
                 open = false;
                 if (tile_idx >= resume) {
-                    if (lane == 0) {
-                        // another CTA filled the output: stop (polled every 32 tiles;
-                        // tiles made meanwhile are discarded by the failed commit)
-                        if (!count_only && (tile_idx & 31u) == 0 && *(volatile unsigned int *)&L.ctl->full) {
-                            trunc = true;
+                    // another CTA filled the output: stop (polled every 128 tiles;
+                    // tiles made meanwhile are discarded by the failed commit)
+                    if (!count_only && (tile_idx & 127u) == 0 && *(volatile unsigned int *)&L.ctl->full) {
+                        trunc = true;
+                    } else {
+                        if (have) {
+                            if (first)
+                                pend.flags |= F_FIRST;
+                            first = false;
+                            if (!push(pend, true))
+                                dead = true;
+                        }
+                        pend = TileDesc{item, tile_idx, 0u, 0u, it.qbeg, it.qlen, qa, cr0, job, jtb, 0u, 0u};
+                        uint32_t nv = 0;
+                        if (full) {
+#pragma unroll
+                            for (int w = 0; w < 8; ++w)
+                                pend.mask[w] = 0xffffffffu;
+                            nv = TC_N;
                         } else {
-                            if (have) {
-                                if (first)
-                                    pend.flags |= F_FIRST;
-                                first = false;
-                                if (!push(pend, true))
-                                    dead = true;
-                            }
-                            pend = TileDesc{item, tile_idx, 0u, 0u, it.qbeg, it.qlen, qa, cr0, job, jtb, 0u, 0u};
-                            uint32_t nv = 0;
 #pragma unroll
                             for (int w = 0; w < 8; ++w) {
-                                pend.mask[w] = S.cmask[w];
-                                nv += __popc(S.cmask[w]);
+                                pend.mask[w] = cm[w];
+                                nv += __popc(cm[w]);
                             }
-                            slots += (unsigned long long)it.qlen * nv;
-                            have = true;
                         }
+                        slots += (unsigned long long)it.qlen * nv;
+                        have = true;
                     }
-                    trunc = __shfl_sync(0xffffffffu, trunc, 0);
-                    dead = __shfl_sync(0xffffffffu, dead, 0);
                 }
                 ++tile_idx;
             };
-            for (int64_t nb0 = nb_begin; nb0 < nb_end && !trunc && !dead; nb0 += 32) {
+            auto pack_window = [&](int64_t s0, const int64_t e0) {   // lane 0 only
+                while (s0 < e0 && !trunc && !dead) {
+                    // whole tiles of a long window: every row valid
+                    if (!open && (s0 & 7) == 0 && e0 - s0 >= TC_N) {
+                        cr0 = (uint32_t)s0;
+                        open = true;
+                        close_tile(true);
+                        s0 += TC_N;
+                        continue;
+                    }
+                    // (windows come in ascending order; one that does not
+                    // starts a tile of its own)
+                    if (open && (s0 >= (int64_t)cr0 + TC_N || s0 < (int64_t)cr0))
+                        close_tile(false);
+                    if (trunc || dead)
+                        return;
+                    if (!open) {
+                        open = true;
+                        cr0 = (uint32_t)(s0 & ~(int64_t)7);
+#pragma unroll
+                        for (int w = 0; w < 8; ++w)
+                            cm[w] = 0u;
+                    }
+                    const int64_t hi = min(e0, (int64_t)cr0 + TC_N);
+                    // rows [s0, hi) of the tile are valid
+                    const int lo_r = (int)(s0 - cr0), hi_r = (int)(hi - cr0);
+#pragma unroll
+                    for (int w = 0; w < 8; ++w) {
+                        const int a = max(lo_r - 32 * w, 0), b = min(hi_r - 32 * w, 32);
+                        if (a < b)
+                            cm[w] |= (b >= 32 ? 0xffffffffu : ((1u << b) - 1u)) & ~((1u << a) - 1u);
+                    }
+                    s0 = hi;
+                    if (s0 < e0)
+                        close_tile(false);   // the window runs on past this tile
+                }
+            };
+            for (int64_t nb0 = nb_begin; nb0 < nb_end; nb0 += 32) {
                 int64_t ws = 0, we = 0;
                 if (nb0 + lane < nb_end) {
                     const uint32_t b = L.ix.adj[nb0 + lane];
@@ -474,37 +510,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
                         we = tc_upper_u(U, ws, we, uhi, ew);
                     }
                 }
-                const int nw = (int)min((int64_t)32, nb_end - nb0);
-                for (int w = 0; w < nw && !trunc && !dead; ++w) {
-                    int64_t s0 = __shfl_sync(0xffffffffu, ws, w);
-                    const int64_t e0 = __shfl_sync(0xffffffffu, we, w);
-                    while (s0 < e0 && !trunc && !dead) {
-                        // (windows come in ascending order; one that does not
-                        // starts a tile of its own)
-                        if (open && (s0 >= (int64_t)cr0 + TC_N || s0 < (int64_t)cr0))
-                            close_tile();
-                        if (trunc || dead)
-                            break;
-                        if (!open) {
-                            open = true;
-                            cr0 = (uint32_t)(s0 & ~(int64_t)7);
-                            if (lane == 0) {
-#pragma unroll
-                                for (int k2 = 0; k2 < 8; ++k2)
-                                    S.cmask[k2] = 0u;
-                            }
-                        }
-                        const int64_t hi = min(e0, (int64_t)cr0 + TC_N);
-                        if (lane == 0)
-                            tc_set_rows(S.cmask, (uint32_t)(s0 - cr0), (uint32_t)(hi - cr0));
-                        s0 = hi;
-                        if (s0 < e0)
-                            close_tile();   // the window runs on past this tile
-                    }
+                S.win[lane][0] = ws;
+                S.win[lane][1] = we;
+                __syncwarp();
+                if (lane == 0) {
+                    const int nw = (int)min((int64_t)32, nb_end - nb0);
+                    for (int w = 0; w < nw && !trunc && !dead; ++w)
+                        pack_window(S.win[w][0], S.win[w][1]);
                 }
+                __syncwarp();
+                trunc = __shfl_sync(0xffffffffu, trunc, 0);
+                dead = __shfl_sync(0xffffffffu, dead, 0);
+                if (trunc || dead)
+                    break;
             }
-            if (!trunc && !dead)
-                close_tile();
+            if (lane == 0 && !trunc && !dead)
+                close_tile(false);
             if (lane == 0 && !dead) {
                 if (have && !trunc) {
                     pend.flags |= F_LAST | (first ? F_FIRST : 0u);
