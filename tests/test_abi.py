@@ -43,6 +43,34 @@ def test_every_declared_symbol_is_exported(lib):
     assert set(gj.EXPORTS) == set(declared_functions())
 
 
+def header_constants():
+    """Every integer #define GJ_... of the header (flags, status codes, limits),
+    evaluated (shifts and ors of earlier names)."""
+    src = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    vals = {}
+    for name, expr in re.findall(r"#define\s+(GJ_[A-Z0-9_]+)\s+([^\n]+)", src):
+        expr = expr.strip().replace("1u", "1")
+        if not expr or name == "GJ_H":
+            continue
+        vals[name] = eval(expr, {}, dict(vals))
+    return vals
+
+
+def test_python_constants_match_the_header():
+    from paper_1809_09930_gb300 import gj
+    consts = header_constants()
+    for must in ("GJ_OK", "GJ_ERR_CAPACITY", "GJ_TC_FILTER", "GJ_HOST_BATCHED", "GJ_DEFAULT_FLAGS"):
+        assert must in consts
+    for name, v in consts.items():
+        if hasattr(gj, name):
+            assert getattr(gj, name) == v, name
+    flags = [n for n in consts if n in ("GJ_REORDER", "GJ_SORTIDU", "GJ_SHORTC", "GJ_TC_FILTER", "GJ_AUTOTUNE",
+                                        "GJ_TUNE_FORM", "GJ_HOST_BATCHED")]
+    assert len(flags) == 7 and all(hasattr(gj, n) for n in flags)
+    bits = [consts[n] for n in flags]
+    assert all(b & (b - 1) == 0 for b in bits) and len(set(bits)) == len(bits)   # distinct single bits
+
+
 def test_host_only_entry_points(lib):
     from paper_1809_09930_gb300 import gj
     assert gj.gj_version().count(".") == 2
