@@ -229,7 +229,10 @@ int gj_self_join_part(gj_index *h, int32_t part, int32_t nparts, gj_pair *pairs_
  *   pairs_out  host or device memory for cap pairs (a = query row, b = entry
  *              row); NULL with cap == 0 counts only
  *   count      out: |Q join_eps E|
- * One kernel launch writes the pairs and counts them.  Returns GJ_OK;
+ * One kernel launch writes the pairs and counts them: into pairs_out directly
+ * when the device can address it (device memory; pinned host memory unless
+ * the index was built with GJ_HOST_BATCHED), else into a device buffer that is
+ * then copied to the host.  Returns GJ_OK;
  * GJ_ERR_CAPACITY when the result exceeds cap (*count holds its size; the
  * buffer holds an unspecified cap of them); GJ_ERR_NONFINITE for a NaN or
  * infinite query coordinate; or another error code.  The eps is the index's.
