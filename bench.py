@@ -58,6 +58,9 @@ def parse():
     ap.add_argument("--dims", default=None, help="comma list of d for the paper-scale workload")
     ap.add_argument("--n", type=int, default=2_000_000)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--ref-budget", type=float, default=None,
+                    help="reference arm: seconds of CPU work per step (default: sized so that the whole "
+                         "run takes about 2.5 minutes, 3-20 s per step)")
     ap.add_argument("--no-baseline", action="store_true", help="skip the CPU oracle leg")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tune", action="store_true",
@@ -231,7 +234,7 @@ def reference_arm(args, runs):
     cb = None
     vals, walls = [], []
     # each step a bounded sample, sized so that the whole run stays near 2.5 minutes
-    budget = max(3.0, min(20.0, 150.0 / max(1, args.warmup + steps)))
+    budget = args.ref_budget or max(3.0, min(20.0, 150.0 / max(1, args.warmup + steps)))
     for _ in range(args.warmup + steps):
         t0 = time.perf_counter()
         cb = cpu_baseline(runs, budget_s=budget)

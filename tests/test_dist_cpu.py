@@ -121,3 +121,22 @@ def test_reference_arm_only_on_rank0():
                         "--warmup", "0"], cwd=ROOT, env=env, capture_output=True, text=True, timeout=120)
     assert r.returncode == 0
     assert r.stdout.strip() == ""
+
+
+def test_reference_arm_prints_the_contract_line():
+    """Rank 0 of the reference arm times the oracle on the host cores and
+    prints one JSON line with the contract's keys (no GPU needed)."""
+    env = {k: v for k, v in os.environ.items() if k not in ("RANK", "WORLD_SIZE", "LOCAL_RANK")}
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "0",
+                        "--ref-budget", "1.5"], cwd=ROOT, env=env, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.strip()]
+    assert len(lines) == 1
+    out = json.loads(lines[0])
+    assert out["impl"] == "reference" and out["value"] > 0 and out["higher_is_better"] is True
+    assert out["steps"] == 1 and out["warmup"] == 0 and out["n_gpus"] == 1
+    assert out["metric"].startswith("distance evals/s") and out["unit"] == "distance evals/s"
+    assert out["e2e"]["value"] == out["value"] and out["e2e"]["h2d_bytes_per_step"] == 0
+    cb = out["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == out["value"] and cb["sample"]
+    assert out["config"]["workload"]
