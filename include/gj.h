@@ -379,6 +379,17 @@ int gj_probe_fp64_tflops(int32_t device, double *tflops);
  * device; returns GJ_OK or an error code. */
 int gj_debug_tc_tile(const uint16_t *A, const uint16_t *B, int32_t Kp, float *D);
 
+/* Diagnostic (no paper counterpart; host only, no device needed): the
+ * tensor-core filter's survivor threshold.  For coordinates scaled by sigma
+ * about a centre and held within radius R0 of it (h = rn16(sigma (x - c))),
+ * every pair within eps has its computed t = |h_a|^2 + |h_b|^2 - 2 <h_a, h_b>
+ * (fp16 products, fp32 accumulation, norms split hi/lo) at most *T.
+ *   eps, sigma  > 0 and finite; R0 >= 0 and finite; 1 <= d <= 124.
+ *   T           out: the fp32 value the kernel compares t with (the bound
+ *               rounded up to fp32).
+ * Returns GJ_OK or GJ_ERR_INVALID_ARG. */
+int gj_tc_threshold(double eps, double sigma, double R0, int32_t d, float *T);
+
 /* Measurement helper (no paper counterpart): number of CUDA kernels this
  * library has launched in this process so far (all handles, all threads). */
 unsigned long long gj_kernel_launches(void);

@@ -1260,3 +1260,16 @@ extern "C" int gj_debug_tc_tile(const uint16_t *A, const uint16_t *B, int32_t Kp
         return GJ_ERR_CUDA;
     return herr ? GJ_ERR_TIMEOUT : GJ_OK;
 }
+
+extern "C" int gj_tc_threshold(double eps, double sigma, double R0, int32_t d, float *T)
+{
+    if (!T || !(eps > 0.0) || !isfinite(eps) || !(sigma > 0.0) || !isfinite(sigma) || !(R0 >= 0.0) ||
+        !isfinite(R0) || d < 1)
+        return GJ_ERR_INVALID_ARG;
+    const int Kp = ((d + 4 + 15) / 16) * 16;
+    if (Kp > 128)
+        return GJ_ERR_INVALID_ARG;
+    const int bits = gj::tc_threshold_bits(eps, sigma, R0, d, Kp);
+    memcpy(T, &bits, sizeof(float));
+    return GJ_OK;
+}

@@ -82,7 +82,7 @@ EXPORTS = ["gj_config_init", "gj_index_build", "gj_index_build_ex", "gj_self_joi
            "gj_last_status", "gj_status_string", "gj_version", "gj_probe_fp64_tflops",
            "gj_kernel_launches", "gj_debug_tc_tile", "gj_self_join_noalloc", "gj_batch_build",
            "gj_batch_self_join", "gj_batch_get_info", "gj_batch_free", "gj_autotune", "gj_batch_get_k",
-           "gj_neighbor_table", "gj_join_qe"]
+           "gj_neighbor_table", "gj_join_qe", "gj_tc_threshold"]
 
 _lib = None
 
@@ -125,6 +125,8 @@ def load(path: str | None = None):
     lib.gj_kernel_launches.argtypes = []
     lib.gj_debug_tc_tile.restype = C.c_int
     lib.gj_debug_tc_tile.argtypes = [V, V, C.c_int32, V]
+    lib.gj_tc_threshold.restype = C.c_int
+    lib.gj_tc_threshold.argtypes = [C.c_double, C.c_double, C.c_double, C.c_int32, C.POINTER(C.c_float)]
     lib.gj_self_join_noalloc.restype = C.c_int
     lib.gj_batch_build.restype = V
     lib.gj_batch_build.argtypes = [C.POINTER(gj_job), C.c_int32, C.POINTER(gj_config)]
@@ -319,6 +321,13 @@ def gj_probe_fp64_tflops(device: int = -1) -> float:
 
 def gj_kernel_launches() -> int:
     return int(load().gj_kernel_launches())
+
+
+def gj_tc_threshold(eps: float, sigma: float, R0: float, d: int) -> tuple[int, float]:
+    """(status, T): the fp32 survivor threshold of the tensor-core filter."""
+    t = C.c_float(0.0)
+    st = load().gj_tc_threshold(float(eps), float(sigma), float(R0), int(d), C.byref(t))
+    return st, t.value
 
 
 def gj_debug_tc_tile(A, B) -> np.ndarray:
