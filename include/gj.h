@@ -59,8 +59,8 @@ extern "C" {
 #define GJ_TC_FILTER  (1u << 3)  /* tensor-core candidate filter + exact FP64 recheck (no paper counterpart) */
 #define GJ_AUTOTUNE   (1u << 4)  /* build: pick k, query block, tile and b_s by timed trials (gj_autotune) */
 #define GJ_TUNE_FORM  (1u << 5)  /* autotune: also try both forms (plain and GJ_TC_FILTER), keep the faster */
-#define GJ_HOST_BATCHED (1u << 6) /* host output always through the result batches of Sec. 3.2.2, even
-                                       where the device can address the host buffer directly */
+#define GJ_HOST_BATCHED (1u << 6) /* host output always through the result batches of Sec. 3.2.2,
+                                   * even where the device can address the host buffer directly */
 #define GJ_DEFAULT_FLAGS (GJ_REORDER | GJ_SORTIDU | GJ_SHORTC)
 
 /* One result pair: original row indices of the two points. */
