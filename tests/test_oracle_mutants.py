@@ -15,7 +15,7 @@ import pytest
 
 import oracle
 import synth
-from tests.test_oracle_pins import full_lattice, lattice_pairs_closed_form
+from tests.test_oracle_pins import full_lattice, lattice_pairs_closed_form, lattice_row
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "gj_oracle.c")
 
@@ -31,6 +31,11 @@ MUTANTS = {
                           "while (stop < e && a->Y[(size_t)a->order[stop] * d + a->u] - ui <= 0.0)"),
     "eps_not_squared": ("    double e2 = eps * eps;\n    brute_arg", "    double e2 = eps;\n    brute_arg"),
     "shortc_wrong_sign": ("        if (s > e2)\n            return s;", "        if (s < e2)\n            return s;"),
+    "query_strict": ("if (gjo_sqdist(X + q * d, X + j * d, d) <= e2) {",
+                     "if (gjo_sqdist(X + q * d, X + j * d, d) < e2) {"),
+    "query_eps_not_squared": ("    double e2 = eps * eps;\n    int64_t c = 0;", "    double e2 = eps;\n    int64_t c = 0;"),
+    "query_row_offset": ("if (gjo_sqdist(X + q * d, X + j * d, d) <= e2) {",
+                         "if (gjo_sqdist(X + q, X + j * d, d) <= e2) {"),
     "qe_strict": ("a->E + j * a->d, a->d) <= a->e2)", "a->E + j * a->d, a->d) < a->e2)"),
     "qe_swapped_orientation": ("kv_push(&a->out, ((uint64_t)i << 32) | (uint64_t)j);\n    return NULL;\n}\n\n/* Every pair",
                                "kv_push(&a->out, ((uint64_t)j << 32) | (uint64_t)i);\n    return NULL;\n}\n\n/* Every pair"),
@@ -85,6 +90,14 @@ def _pins_pass() -> bool:
         w4 = np.argwhere((dq * dq).sum(-1) <= 4).astype(np.uint32)
         if not np.array_equal(oracle.brute_qe(Qz, Ez, 2.0), w4):
             return False
+        # one point's neighbours (the full-size tests' checker) on the lattice,
+        # at an exact boundary (eps = 2) and away from the first row
+        Xl = full_lattice(4, 3)
+        for q in (0, 21, 42, 63):
+            for eps, E in ((2.0, 4), (1.0, 1)):
+                got = oracle.query_neighbors(Xl, eps, q).astype(np.int64)
+                if not np.array_equal(got, lattice_row(Xl[q].astype(np.int64), 4, E)):
+                    return False
         return True
     except (MemoryError, ValueError):
         return False

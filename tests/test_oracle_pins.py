@@ -303,3 +303,41 @@ def test_qe_orientation_and_far_sets():
     assert oracle.brute_qe(Q, E, 1.0).tolist() == [[0, 0], [1, 2]]
     assert oracle.brute_qe(Q + 100.0, E, 1.0).size == 0
     assert oracle.brute_qe(np.zeros((0, 1)), E, 1.0).size == 0
+
+
+# ---------------------------------------------------------------------------
+# One point's neighbours by the definition (Sec. 3.1): the checker the
+# full-size tests use per sampled query.  On the full integer lattice each row
+# is known independently (lattice_row); on a random lattice subset exact
+# integer arithmetic decides every pair; at eps = 2 and 3 the boundary is
+# exact, so a strict comparison or an unsquared eps changes the row.
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("L,d", [(4, 3), (5, 2), (3, 4)])
+@pytest.mark.parametrize("eps,E", [(1.0, 1), (math.sqrt(2.0), 2), (2.0, 4), (3.0, 9)])
+def test_query_neighbors_rows_on_the_lattice(L, d, eps, E):
+    X = full_lattice(L, d)
+    for q in range(len(X)):
+        got = oracle.query_neighbors(X, eps, q).astype(np.int64)
+        assert np.array_equal(got, lattice_row(X[q].astype(np.int64), L, E)), q
+
+
+def test_query_neighbors_exact_integer_reference():
+    X = synth.lattice(500, 6, seed=13, side=5)
+    Xi = X.astype(np.int64)
+    for q in (0, 1, 77, 250, 499):
+        dif = Xi - Xi[q]
+        sq = (dif * dif).sum(-1)
+        for eps, E2 in ((1.0, 1), (2.0, 4), (math.sqrt(5.0) * (1 + 1e-12), 5)):
+            want = np.flatnonzero(sq <= E2)
+            assert np.array_equal(oracle.query_neighbors(X, eps, q).astype(np.int64), want)
+
+
+@pytest.mark.parametrize("kind", ["uniform", "mixture", "skewed"])
+def test_query_neighbors_equal_the_rows_of_the_nested_loop(kind):
+    X = synth.generate(kind, 1500, 9, 21)
+    eps = {"uniform": 0.45, "mixture": 0.12, "skewed": 0.15}[kind]
+    pairs = oracle.brute(X, eps)
+    for q in (0, 3, 700, 1499):
+        want = pairs[pairs[:, 0] == q, 1]
+        assert np.array_equal(oracle.query_neighbors(X, eps, q), want), q
