@@ -151,6 +151,37 @@ def rank_sum(dist, xs: list, device: str = "cuda") -> list:
     return [int(v) for v in t.tolist()]
 
 
+def settings_of(t) -> dict:
+    """Index settings from one autotuner pick (None: the analytic k)."""
+    if not t:
+        return {"k": 0}
+    return {"k": t["k"], "query_block": t["query_block"], "tile": t["tile"]}
+
+
+def agree(dist, obj):
+    """Rank 0's value of obj on every rank.  The autotuner times trials, so
+    two ranks tuning on their own may pick different k or query blocks; the
+    entity partition deals parts of one load-ordered item list, so every rank
+    must build with the same picks (Sec. 6.2)."""
+    if dist is None:
+        return obj
+    box = [obj]
+    dist.broadcast_object_list(box, src=0)
+    return box[0]
+
+
+def check_same(dist, obj, what: str) -> None:
+    """Raise on every rank unless all ranks hold an equal obj (e.g. the number
+    of work items per d: parts dealt from different item lists would overlap
+    or miss pairs without any other error)."""
+    if dist is None:
+        return
+    objs = [None] * dist.get_world_size()
+    dist.all_gather_object(objs, obj)
+    if any(o != objs[0] for o in objs):
+        raise RuntimeError(f"ranks disagree on {what}: {objs}")
+
+
 # The paper's synthetic sets (Sec. 5.1: i.i.d. exponential, lambda = 40, 2e6
 # points) at the largest eps its Table 4 lists for each (Table 2 times
 # Syn16D2M at eps = 0.05).
@@ -526,22 +557,23 @@ def main():
 
     # autotuner: k, query block and tile per d by timed trials, once, before
     # the warm-up; every step then builds with the picks
+    # (rank 0 tunes; every rank builds with its picks)
     tuned = {}
     tune_s = 0.0
     if not args.no_tune:
         t0 = time.perf_counter()
-        for r, X, Xd in data:
-            tcfg = gj.gj_config_init()
-            tcfg.flags = flags
-            tcfg.stream = stream.cuda_stream
-            tuned[r["d"]] = gj.gj_autotune(Xd, r["eps"], tcfg)
+        if rank == 0:
+            for r, X, Xd in data:
+                tcfg = gj.gj_config_init()
+                tcfg.flags = flags
+                tcfg.stream = stream.cuda_stream
+                tuned[r["d"]] = gj.gj_autotune(Xd, r["eps"], tcfg)
+        tuned = agree(dist, tuned)
         tune_s = time.perf_counter() - t0
+    check_same(dist, {d: settings_of(t) for d, t in tuned.items()}, "the tuned settings")
 
     def settings(d):
-        t = tuned.get(d)
-        if not t:
-            return {"k": 0}
-        return {"k": t["k"], "query_block": t["query_block"], "tile": t["tile"]}
+        return settings_of(tuned.get(d))
 
     def one_step(collect):
         tot_evals = 0
@@ -565,6 +597,7 @@ def main():
             collect["evaluated"] += s["evaluated"]
             collect["pairs"][r["d"]] = cnt
             collect["k"][r["d"]] = info["k"]
+            collect["items"][r["d"]] = info["work_items"]
             collect["flops"] += 2.0 * r["d"] * info["candidate_pairs"] / world
             collect["survivors"] += s["tc_survivors"]
             tot_evals += info["candidate_pairs"]
@@ -573,11 +606,13 @@ def main():
 
     def fresh():
         return {"cap": {}, "out": {}, "join_ms": 0.0, "launches_join": 0, "dims": 0, "evaluated": 0,
-                "pairs": {}, "k": {}, "flops": 0.0, "survivors": 0, "join_ms_d": {}}
+                "pairs": {}, "k": {}, "items": {}, "flops": 0.0, "survivors": 0, "join_ms_d": {}}
 
     col = fresh()
     for _ in range(args.warmup):
         one_step(col)
+    if args.warmup:
+        check_same(dist, col["items"], "the work items per d")
     fp64_tflops = gj.gj_probe_fp64_tflops()
 
     keep = {"cap": col["cap"], "out": col["out"]}
@@ -602,6 +637,8 @@ def main():
     launches = gj.gj_kernel_launches() - l0
     clk = clocks.stop()
     ms = rank_max(dist, ev0.elapsed_time(ev1))
+    if not args.warmup:
+        check_same(dist, col["items"], "the work items per d")
     ds = sorted(col["pairs"])
     col["pairs"] = dict(zip(ds, rank_sum(dist, [col["pairs"][d] for d in ds])))
     # evals: the whole job's candidate pairs (parts of one join sum to the join)

@@ -2,7 +2,8 @@
 
 Entity partitioning (Sec. 6.2) needs no exchange of data; the ranks only
 agree on the step time (the slowest rank) and add up their parts' pair
-counts.  These tests run the bench's own reduction helpers across two gloo
+counts, and they build with one set of autotuner picks (rank 0's, broadcast).
+These tests run the bench's own reduction and agreement helpers across two gloo
 processes, check the oracle's view of the partition (parts of the query
 blocks dealt round-robin are disjoint and their union is R), and check that
 the reference arm runs on rank 0 only.
@@ -102,6 +103,46 @@ def _part_pairs(X, eps, k, part, nparts):
                     out.add((i, j))
                     out.add((j, i))
     return out
+
+
+def _pick_worker(rank, world, port, q):
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    # each rank's own (timing-based) pick differs; the helper hands every rank rank 0's
+    own = {16: {"k": 4 + 3 * rank, "query_block": 120 - 56 * rank, "tile": 64, "batch_pairs": 0,
+                "trials": 12}}
+    picked = bench.agree(dist, own)
+    bench.check_same(dist, {d: bench.settings_of(t) for d, t in picked.items()}, "the tuned settings")
+    # ranks whose item lists differ must fail loudly, on every rank
+    try:
+        bench.check_same(dist, {16: 1000 + rank}, "the work items per d")
+        raised = False
+    except RuntimeError:
+        raised = True
+    dist.barrier()
+    dist.destroy_process_group()
+    q.put((rank, picked, raised))
+
+
+def test_ranks_build_with_rank0_picks_gloo_world2():
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    ps = [ctx.Process(target=_pick_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in ps:
+        p.start()
+    res = sorted((r for r in (q.get(timeout=120) for _ in ps)), key=lambda x: x[0])
+    for p in ps:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, picked, raised in res:
+        assert picked == {16: {"k": 4, "query_block": 120, "tile": 64, "batch_pairs": 0, "trials": 12}}
+        assert raised
 
 
 def test_entity_partition_parts_are_disjoint_and_cover_R():
