@@ -183,7 +183,7 @@ def check_same(dist, obj, what: str) -> None:
 
 
 # The paper's synthetic sets (Sec. 5.1: i.i.d. exponential, lambda = 40, 2e6
-# points) at the largest eps its Table 4 lists for each (Table 2 times
+# points) at the largest eps its Table 3 lists for each (Table 2 times
 # Syn16D2M at eps = 0.05).
 SYN_EPS = {16: 0.05, 32: 0.10, 64: 0.18}
 
@@ -191,7 +191,7 @@ SYN_EPS = {16: 0.05, 32: 0.10, 64: 0.18}
 def workload_name(args, runs) -> str:
     if args.workload == "exponential":
         return (f"paper's Syn16/32/64D2M shape: exponential (lambda=40) [0,1]^d, n={args.n}, "
-                f"d in {[r['d'] for r in runs]}, eps {[r['eps'] for r in runs]} (Table 4)")
+                f"d in {[r['d'] for r in runs]}, eps {[r['eps'] for r in runs]} (Table 3)")
     return (f"paper-scale uniform [0,1)^d, n={args.n}, d in {[r['d'] for r in runs]}, "
             f"eps for 32 mean neighbours")
 

@@ -195,7 +195,8 @@ int gj_autotune(const double *points, int64_t n, int32_t d, double eps, const gj
  *   cap        capacity of pairs_out in pairs.
  *   count      out: |R| (always the full size, also on GJ_ERR_CAPACITY).
  * Returns GJ_OK, or GJ_ERR_CAPACITY when |R| > cap (the contents of pairs_out
- * are then unspecified), or another error code.  Pageable host output is
+ * are then unspecified), GJ_ERR_INVALID_ARG when pairs_out is device memory of
+ * another device, or another error code.  Pageable host output is
  * copied in result batches (Sec. 3.2.2) on a second stream while the next
  * batch runs.  Pinned host memory that the device can address (cudaMallocHost,
  * cudaHostAlloc, mapped cudaHostRegister; CUDA reports a device pointer for
@@ -224,10 +225,11 @@ int gj_self_join_part(gj_index *h, int32_t part, int32_t nparts, gj_pair *pairs_
  * and by E's SORTIDU dimension; each query cell searches all adjacent
  * non-empty entry cells; distances are the FP64 SHORTC sums of the self-join.
  *   h          an index over E (any flags; the join uses the plain FP64 form)
- *   queries    row-major nq x d FP64 (d = E's), host or device memory;
- *              copied, the caller keeps ownership
- *   pairs_out  host or device memory for cap pairs (a = query row, b = entry
- *              row); NULL with cap == 0 counts only
+ *   queries    row-major nq x d FP64 (d = E's), host or device memory (of
+ *              any device); copied, the caller keeps ownership
+ *   pairs_out  host memory or device memory of the handle's device for cap
+ *              pairs (a = query row, b = entry row); another device's memory
+ *              returns GJ_ERR_INVALID_ARG; NULL with cap == 0 counts only
  *   count      out: |Q join_eps E|
  * One kernel launch writes the pairs and counts them: into pairs_out directly
  * when the device can address it (device memory; pinned host memory unless
@@ -264,7 +266,9 @@ int gj_neighbor_table(gj_index *h, int64_t *row_start, uint32_t *nbr, uint64_t c
  * entering the driver's allocator during a join, cannot accept that; this entry
  * point serves them.  It runs the plain FP64 join (not the tensor-core filter)
  * and writes pairs straight into pairs_out, which must be device memory of the
- * handle's device (NULL with cap == 0: count only).  Its scratch -- the
+ * handle's device, else GJ_ERR_INVALID_ARG (NULL with cap == 0: count only; a
+ * non-NULL pairs_out with cap == 0 writes nothing and returns GJ_ERR_CAPACITY
+ * with *count = |R| when |R| > 0).  Its scratch -- the
  * control block and the dequeue order of the part's work items -- lives in one
  * 4 MiB array in device global memory that the library declares at file scope;
  * every GPU that loads the library holds that array until the process exits.
@@ -274,8 +278,11 @@ int gj_neighbor_table(gj_index *h, int64_t *row_start, uint32_t *nbr, uint64_t c
  *                    parts return GJ_ERR_TOO_LARGE.  Indices built with
  *                    GJ_TC_FILTER return GJ_ERR_INVALID_ARG.
  *   set-up           the first call on a device looks up the array's device
- *                    address (cudaGetSymbolAddress) with that device current;
- *                    make that first call before any stream capture.
+ *                    address (cudaGetSymbolAddress) with that device current,
+ *                    and so does the first call after that device's context
+ *                    was reset; make that first call before any stream
+ *                    capture.  The call is synchronous: it returns once the
+ *                    join has finished on the handle's stream.
  *   sharing          all calls share the array and find the last call's
  *                    contents (the call clears what must start at zero).
  *                    Calls that overlap on the GPU race on it: do not run two

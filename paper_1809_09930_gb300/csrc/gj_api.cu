@@ -60,6 +60,24 @@ gj_pair *device_view(gj_pair *p, bool allow_host)
         return static_cast<gj_pair *>(a.devicePointer);
     return nullptr;
 }
+bool device_memory_of(const void *p, int device)
+{
+    cudaPointerAttributes a{};
+    if (!p || cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return (a.type == cudaMemoryTypeDevice && a.device == device) || a.type == cudaMemoryTypeManaged;
+}
+bool foreign_device(const void *p, int device)
+{
+    cudaPointerAttributes a{};
+    if (!p || cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice && a.device != device;
+}
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 unsigned long long launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
 }  // namespace gj
@@ -239,6 +257,8 @@ int join_impl(gj_index *h, int part, int nparts, gj_pair *pairs_out, uint64_t ca
     cudaError_t e = cudaSetDevice(h->device);
     if (e != cudaSuccess)
         return cuda_status(e);
+    if (pairs_out && foreign_device(pairs_out, h->device))
+        return GJ_ERR_INVALID_ARG;   // another device's memory
     cudaStream_t s = h->stream;
     const int64_t nitems = h->nitems;
     const int64_t nq = nitems > part ? (nitems - part + nparts - 1) / nparts : 0;

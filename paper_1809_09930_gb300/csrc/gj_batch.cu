@@ -592,15 +592,8 @@ int gj_batch_self_join(gj_batch *b, gj_pair *const *outs, const uint64_t *caps, 
         const uint64_t c = caps ? caps[j] : 0;
         if (!o && c > 0)
             return GJ_ERR_INVALID_ARG;
-        if (o) {
-            cudaPointerAttributes a{};
-            if (cudaPointerGetAttributes(&a, o) != cudaSuccess) {
-                cudaGetLastError();
-                return GJ_ERR_INVALID_ARG;
-            }
-            if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)
-                return GJ_ERR_INVALID_ARG;
-        }
+        if (o && !device_memory_of(o, b->device))
+            return GJ_ERR_INVALID_ARG;   // not device memory of the batch's device
         b->jobs_host[j].out = c ? o : nullptr;
         b->jobs_host[j].cap = c;
     }

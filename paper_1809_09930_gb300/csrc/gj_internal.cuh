@@ -138,6 +138,13 @@ void pool_keep(int device);
 // it is; pinned host memory through the device pointer CUDA reports for it
 // (when allow_host); nullptr for pageable host memory.
 gj_pair *device_view(gj_pair *p, bool allow_host);
+// Device memory of `device` itself, or managed memory: a buffer the kernels of
+// a handle on `device` may read and write.
+bool device_memory_of(const void *p, int device);
+// Device memory of another device: the kernels of a handle on `device` must
+// not touch it (without peer access that is an illegal address), so the entry
+// points reject it with GJ_ERR_INVALID_ARG.
+bool foreign_device(const void *p, int device);
 
 // Count of kernels this library has launched (process-wide); read through
 // gj_kernel_launches().

@@ -11,6 +11,7 @@
 // -- the control block and the work-item order -- in one file-scope
 // __device__ array of fixed size, which every GPU that loads the library holds
 // until the process exits.
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
@@ -34,25 +35,63 @@ static_assert(sizeof(gj::JoinCtl) <= kCtlBytes, "control block does not fit its 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 std::mutex g_mu;
-void *g_scratch_addr[kMaxDevices] = {};
+struct ScratchAt {
+    unsigned long long ctx;   // unique id of the context the address belongs to
+    void *addr;
+};
+ScratchAt g_scratch_at[kMaxDevices] = {};
 
-// Device address of the scratch on `dev`, looked up once per device with that
-// device current (the first call on a device does this set-up).
+// Unique id of the calling thread's current context (0 when unknown).  A
+// device reset destroys the context the cached address belongs to, and the
+// next context on that device gets a new id.
+unsigned long long current_context_id()
+{
+    using GetCurrent = CUresult (*)(CUcontext *);
+    using GetId = CUresult (*)(CUcontext, unsigned long long *);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<GetCurrent>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<GetId>(f);
+        cudaGetLastError();
+    });
+    CUcontext c = nullptr;
+    unsigned long long id = 0;
+    if (!get_current || !get_id || get_current(&c) != CUDA_SUCCESS || !c || get_id(c, &id) != CUDA_SUCCESS)
+        return 0;
+    return id;
+}
+
+// Device address of the scratch on `dev` (the current device), looked up with
+// cudaGetSymbolAddress once per device and context: the first call on a
+// device, and the first after that device's context was reset, does this
+// set-up.  (With no context id available it is looked up on every call.)
 int scratch_address(int dev, unsigned char **out)
 {
     if (dev < 0 || dev >= kMaxDevices)
         return GJ_ERR_UNSUPPORTED;
+    const unsigned long long ctx = current_context_id();
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_scratch_addr[dev]) {
+    ScratchAt &at = g_scratch_at[dev];
+    if (!at.addr || ctx == 0 || at.ctx != ctx) {
         void *p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || p == nullptr) {
             cudaGetLastError();
             return GJ_ERR_CUDA;
         }
-        g_scratch_addr[dev] = p;
+        at.addr = p;
+        at.ctx = ctx;
     }
-    *out = static_cast<unsigned char *>(g_scratch_addr[dev]);
+    *out = static_cast<unsigned char *>(at.addr);
     return GJ_OK;
 }
 
@@ -79,15 +118,8 @@ extern "C" int gj_self_join_noalloc(const gj_index *h, int32_t part, int32_t npa
         cudaGetLastError();
         return GJ_ERR_CUDA;
     }
-    if (pairs_out) {
-        cudaPointerAttributes a{};
-        if (cudaPointerGetAttributes(&a, pairs_out) != cudaSuccess) {
-            cudaGetLastError();
-            return GJ_ERR_INVALID_ARG;
-        }
-        if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)
-            return GJ_ERR_INVALID_ARG;   // the output must be device memory
-    }
+    if (pairs_out && !device_memory_of(pairs_out, h->device))
+        return GJ_ERR_INVALID_ARG;   // the output must be device memory of the handle's device
     const int64_t nitems = h->nitems;
     const int64_t nq = nitems > part ? (nitems - part + nparts - 1) / nparts : 0;
     if ((uint64_t)nq > kMaxItems)
@@ -145,6 +177,8 @@ extern "C" int gj_self_join_noalloc(const gj_index *h, int32_t part, int32_t npa
         cudaGetLastError();
         return GJ_ERR_CUDA;
     }
+    if (res.err & kErrTimeout)
+        return GJ_ERR_TIMEOUT;
     if (res.err)
         return GJ_ERR_CUDA;
     const uint64_t total = cap ? res.pos : res.counted;

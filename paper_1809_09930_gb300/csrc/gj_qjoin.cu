@@ -40,16 +40,6 @@ int status_of(cudaError_t e)
     return e == cudaErrorMemoryAllocation ? GJ_ERR_OOM : GJ_ERR_CUDA;
 }
 
-bool device_memory(const void *p)
-{
-    cudaPointerAttributes a{};
-    if (!p || cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
-
 }  // namespace
 }  // namespace gj
 
@@ -65,6 +55,8 @@ extern "C" int gj_join_qe(gj_index *h, const double *queries, int64_t nq, gj_pai
     *count = 0;
     if (cudaSetDevice(h->device) != cudaSuccess)
         return GJ_ERR_CUDA;
+    if (pairs_out && foreign_device(pairs_out, h->device))
+        return GJ_ERR_INVALID_ARG;   // another device's memory
     cudaStream_t s = h->stream;
     const int d = h->info.d;
     // query blocks small enough that every CTA of the persistent grid gets
@@ -82,12 +74,13 @@ extern "C" int gj_join_qe(gj_index *h, const double *queries, int64_t nq, gj_pai
     double *Qd = nullptr;
     unsigned int *flag = nullptr;
     unsigned int hflag = 0;
-    const bool q_on_dev = device_memory(queries);
+    // host memory or another device's memory is copied to this device first
+    const bool q_on_dev = device_memory_of(queries, h->device);
     cudaError_t e = cudaSuccess;
     if (nq > 0 && !q_on_dev) {
         e = cudaMalloc(&Qd, (size_t)nq * d * sizeof(double));
         if (e == cudaSuccess)
-            e = cudaMemcpyAsync(Qd, queries, (size_t)nq * d * sizeof(double), cudaMemcpyHostToDevice, s);
+            e = cudaMemcpyAsync(Qd, queries, (size_t)nq * d * sizeof(double), cudaMemcpyDefault, s);
     }
     const double *Q = (nq > 0 && !q_on_dev) ? Qd : queries;
     if (e == cudaSuccess) e = cudaMalloc(&flag, sizeof(unsigned int));

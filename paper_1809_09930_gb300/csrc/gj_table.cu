@@ -51,16 +51,6 @@ int status_of(cudaError_t e)
     return e == cudaErrorMemoryAllocation ? GJ_ERR_OOM : GJ_ERR_CUDA;
 }
 
-bool on_device(const void *p)
-{
-    cudaPointerAttributes a{};
-    if (!p || cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
-
 }  // namespace
 }  // namespace gj
 
@@ -73,7 +63,7 @@ extern "C" int gj_neighbor_table(gj_index *h, int64_t *row_start, uint32_t *nbr,
     *count = 0;
     if (cudaSetDevice(h->device) != cudaSuccess)
         return GJ_ERR_CUDA;
-    if (!on_device(row_start) || (cap > 0 && !on_device(nbr)))
+    if (!device_memory_of(row_start, h->device) || (cap > 0 && !device_memory_of(nbr, h->device)))
         return GJ_ERR_INVALID_ARG;
     const int64_t n = h->info.n;
     cudaStream_t s = h->stream;

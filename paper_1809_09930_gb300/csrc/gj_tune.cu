@@ -194,14 +194,12 @@ int autotune_impl(const double *points, int64_t n, int d, double eps, const gj_c
     if (e != cudaSuccess)
         return GJ_ERR_UNSUPPORTED;
     base.device = device;
-    cudaPointerAttributes pa{};
-    const bool on_dev = n > 0 && cudaPointerGetAttributes(&pa, points) == cudaSuccess &&
-                        (pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged);
-    cudaGetLastError();
+    // host memory or another device's memory is copied to this device first
+    const bool on_dev = n > 0 && device_memory_of(points, device);
     if (n > 0 && !on_dev) {
         e = cudaMalloc(&Pdev, (size_t)n * d * sizeof(double));
         if (e == cudaSuccess)
-            e = cudaMemcpy(Pdev, points, (size_t)n * d * sizeof(double), cudaMemcpyHostToDevice);
+            e = cudaMemcpy(Pdev, points, (size_t)n * d * sizeof(double), cudaMemcpyDefault);
         if (e != cudaSuccess) {
             cudaFree(Pdev);
             return e == cudaErrorMemoryAllocation ? GJ_ERR_OOM : GJ_ERR_CUDA;

@@ -10,6 +10,8 @@ scratch contents) and check it against gj_self_join on the same index.  The
 file sorts last so that a run stopping at the first failure has run every
 other test before it.
 """
+import ctypes as C
+
 import numpy as np
 import pytest
 
@@ -76,3 +78,28 @@ def test_noalloc_rejects_host_output_and_too_many_work_items():
         assert ix.info()["work_items"] > 1_048_512
         st, _ = gj.gj_self_join_noalloc(ix.h, None)
         assert st == gj.GJ_ERR_TOO_LARGE
+
+
+def test_noalloc_rejects_a_tensor_core_index_and_counts_into_a_zero_capacity_buffer():
+    X = synth.uniform(3000, 8, 44)
+    with gj.Index(X, 0.3, k=2, flags=gj.GJ_DEFAULT_FLAGS | gj.GJ_TC_FILTER) as ix:
+        st, _ = gj.gj_self_join_noalloc(ix.h, None)
+        assert st == gj.GJ_ERR_INVALID_ARG          # tensor-core indices use gj_self_join
+    with gj.Index(X, 0.3, k=2) as ix:
+        n = ix.count()
+        assert n > 0
+        buf = torch.full((1, 2), -1, dtype=torch.int32, device="cuda")
+        cnt = C.c_uint64(0)
+        st = gj.load().gj_self_join_noalloc(ix.h, 0, 1, buf.data_ptr(), 0, C.byref(cnt))
+        assert st == gj.GJ_ERR_CAPACITY and cnt.value == n    # non-NULL, cap 0: counted, nothing written
+        assert int(buf.min().item()) == -1
+
+
+@pytest.mark.skipif(not torch.cuda.is_available() or torch.cuda.device_count() < 2,
+                    reason="needs a second visible device")
+def test_noalloc_rejects_another_devices_buffer():
+    X = synth.uniform(2000, 4, 45)
+    with gj.Index(X, 0.2, k=2) as ix:
+        other = torch.empty((10, 2), dtype=torch.int32, device="cuda:1")
+        st, _ = gj.gj_self_join_noalloc(ix.h, other)     # checked on the host, nothing launched
+        assert st == gj.GJ_ERR_INVALID_ARG
