@@ -219,7 +219,7 @@ int run_launch(gj_index *h, JoinBuffers &B, JoinLaunch L, int grid, JoinCtl init
     L.ctl = B.ctl;
     L.sm_span = B.span;
     cudaEventRecord(B.ev_k0, s);
-    e = h->tc_ready ? launch_join_tc(h, L, grid, s) : launch_join_plain(L, grid, s);
+    e = h->tc_ready ? launch_join_tc(h, L, grid, s, false) : launch_join_plain(L, grid, s);
     if (e != cudaSuccess)
         return cuda_status(e);
     cudaEventRecord(B.ev_k1, s);
@@ -244,6 +244,95 @@ int run_launch(gj_index *h, JoinBuffers &B, JoinLaunch L, int grid, JoinCtl init
     }
     if (result->err & kErrTimeout)
         return GJ_ERR_TIMEOUT;
+    return GJ_OK;
+}
+
+void free_direct_state(gj_index *h)
+{
+    cudaFree(h->jd_ctl);
+    cudaFreeHost(h->jd_hctl);
+    cudaFree(h->jd_queue);
+    cudaFree(h->jd_span);
+    cudaFreeHost(h->jd_hspan);
+    if (h->jd_ev0)
+        cudaEventDestroy(h->jd_ev0);
+    if (h->jd_ev1)
+        cudaEventDestroy(h->jd_ev1);
+    h->jd_ctl = h->jd_hctl = nullptr;
+    h->jd_queue = nullptr;
+    h->jd_span = h->jd_hspan = nullptr;
+    h->jd_ev0 = h->jd_ev1 = nullptr;
+    h->jd_ready = false;
+}
+
+// The tensor-core join's direct form: one launch over the part's work items
+// that writes pairs straight into `out` (device-addressable, cap pairs; pairs
+// past cap are counted, not written) or, with out == nullptr, only counts.
+// No estimate, batches, staging or resume: the output either holds R or the
+// call reports GJ_ERR_CAPACITY with |R|.  The launch state lives on the handle.
+int join_tc_direct(gj_index *h, int part, int nparts, int64_t nq, int grid, gj_pair *out, uint64_t cap,
+                   uint64_t *total)
+{
+    cudaStream_t s = h->stream;
+    cudaError_t e = cudaSuccess;
+    if (!h->jd_ready) {
+        e = cudaMalloc(&h->jd_ctl, sizeof(JoinCtl));
+        if (e == cudaSuccess) e = cudaMallocHost(&h->jd_hctl, sizeof(JoinCtl));
+        if (e == cudaSuccess) e = cudaMalloc(&h->jd_queue, (size_t)std::max<int64_t>(h->nitems, 1) * sizeof(uint32_t));
+        if (e == cudaSuccess) e = cudaMalloc(&h->jd_span, 2 * kSmSlots * sizeof(unsigned long long));
+        if (e == cudaSuccess) e = cudaMallocHost(&h->jd_hspan, 2 * kSmSlots * sizeof(unsigned long long));
+        if (e == cudaSuccess) e = cudaEventCreate(&h->jd_ev0);
+        if (e == cudaSuccess) e = cudaEventCreate(&h->jd_ev1);
+        if (e != cudaSuccess) {
+            free_direct_state(h);
+            return cuda_status(e);
+        }
+        h->jd_ready = true;
+    }
+    note_launch();
+    k_gather_queue<<<(int)((nq + 255) / 256), 256, 0, s>>>(h->order, part, nparts, nq, 1, h->jd_queue);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->jd_ctl, 0, sizeof(JoinCtl), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->jd_span, 0, 2 * kSmSlots * sizeof(unsigned long long), s);
+    if (e != cudaSuccess)
+        return cuda_status(e);
+    JoinLaunch L{};
+    L.ix = view_of(h);
+    L.queue = h->jd_queue;
+    L.qlimit = (uint32_t)nq;
+    L.ctl = h->jd_ctl;
+    L.sm_span = h->jd_span;
+    L.out = out;
+    L.cap = out ? cap : 0;
+    cudaEventRecord(h->jd_ev0, s);
+    e = launch_join_tc(h, L, grid, s, true);
+    if (e != cudaSuccess)
+        return cuda_status(e);
+    cudaEventRecord(h->jd_ev1, s);
+    e = cudaMemcpyAsync(h->jd_hctl, h->jd_ctl, sizeof(JoinCtl), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->jd_hspan, h->jd_span, 2 * kSmSlots * sizeof(unsigned long long),
+                            cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess)
+        return cuda_status(e);
+    const JoinCtl res = *h->jd_hctl;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, h->jd_ev0, h->jd_ev1);
+    *total = out ? res.pos : res.counted;
+    h->last.pairs = *total;
+    h->last.launches = 1;
+    h->last.join_ms = ms;
+    h->last.busy_ms = mean_sm_span_ms(h->jd_hspan);
+    h->last.tc_survivors = res.survivors;
+    h->last.evaluated = res.evaluated;
+    h->last.dims = res.dims;
+    h->last.batches_planned = 1;
+    if (res.err & kErrTimeout)
+        return GJ_ERR_TIMEOUT;
+    if (res.err)
+        return GJ_ERR_CUDA;
     return GJ_OK;
 }
 
@@ -278,6 +367,16 @@ int join_impl(gj_index *h, int part, int nparts, gj_pair *pairs_out, uint64_t ca
     gj_pair *const direct = device_view(pairs_out, !(h->cfg.flags & GJ_HOST_BATCHED));
     const bool dev_out = direct != nullptr;
     const bool count_only_call = (cap == 0);
+
+    if (h->tc_ready && (dev_out || count_only_call)) {
+        uint64_t total = 0;
+        const int st = join_tc_direct(h, part, nparts, nq, grid, count_only_call ? nullptr : direct, cap, &total);
+        *count = total;
+        h->last.total_ms = now_ms() - t_start;
+        if (st != GJ_OK)
+            return st;
+        return total > cap ? GJ_ERR_CAPACITY : GJ_OK;
+    }
 
     JoinBuffers B;
 #define TRYC(x)                                                     \
@@ -671,6 +770,10 @@ void gj_free(gj_index *h)
     dev_free(h->XB, s);
     dev_free(h->tc_centre, s);
     dev_free(h->perm_dev, s);
+    if (h->jd_ready) {
+        cudaStreamSynchronize(s);
+        free_direct_state(h);
+    }
     if (h->drain_stream)
         cudaStreamDestroy(h->drain_stream);
     if (h->own_stream && h->stream)

@@ -191,7 +191,10 @@ struct TcJob {
 
 // ---- tensor-core filter (gj_tc.cu) -----------------------------------------
 int tc_prepare(gj_index *h, const double *stats_host, const int *perm, cudaStream_t s);
-cudaError_t launch_join_tc(const gj_index *h, const JoinLaunch &L, int grid, cudaStream_t s);
+// direct = true: pairs straight into L.out (device-addressable) with one
+// reservation per warp, no staging and no resume (L.ctl->pos counts every
+// pair, written or not); false: per-CTA staging committed per work item.
+cudaError_t launch_join_tc(const gj_index *h, const JoinLaunch &L, int grid, cudaStream_t s, bool direct);
 size_t tc_staging_pairs_per_cta();
 int tc_threshold_bits(double eps, double sigma, double R0, int d, int Kp);
 cudaError_t tc_pack_into(const double *X, int64_t n, int64_t npad, int d, int Kp, double sigma, const double *centre,
@@ -272,4 +275,11 @@ struct gj_index {
     int tc_Tbits;        // fp32 bits of the survivor threshold (scaled units)
     double tc_sigma, tc_R0;
     double *tc_centre;   // device, the filter's centre per reordered dimension
+    // launch state of the tensor-core join's direct form, allocated by the
+    // first such join on the handle and kept until gj_free
+    bool jd_ready;
+    gj::JoinCtl *jd_ctl, *jd_hctl;          // device, pinned host
+    uint32_t *jd_queue;                      // device, one entry per work item
+    unsigned long long *jd_span, *jd_hspan;  // per-SM spans: device, pinned host
+    cudaEvent_t jd_ev0, jd_ev1;
 };

@@ -54,7 +54,7 @@ namespace gj {
 
 using namespace sm100;
 
-constexpr int TC_THREADS = 320;
+constexpr int TC_THREADS = 352;
 constexpr int TC_N = 256;        // candidate rows per tile (one M=128 x N=256 MMA per K step)
 constexpr int TC_M = 128;        // query rows per A tile
 constexpr int TC_DR = 16;        // descriptor ring entries
@@ -62,14 +62,16 @@ constexpr uint32_t TC_STG = 1u << 18;   // staging pairs per half per CTA (4 til
 constexpr uint64_t TC_LIMIT_NS = 4000000000ull;   // 4 s per wait
 constexpr int TC_SQ = 64;        // survivor queue per epilogue warp
 
-enum : uint32_t { F_FIRST = 1, F_LAST = 2, F_MARKER = 4, F_TRUNC = 8, F_TERM = 16, F_FLUSH = 64 };
+// F_PAD: a no-op turn after an item that made one turn only, so that every
+// item has a turn of each parity (each MMA issuer sees every item)
+enum : uint32_t { F_FIRST = 1, F_LAST = 2, F_MARKER = 4, F_TRUNC = 8, F_TERM = 16, F_PAD = 32, F_FLUSH = 64 };
 
 // One candidate tile: rows r0 .. r0+255 of the B operand, of which the rows
 // in the searched windows are valid (bit c of mask = row r0 + c).  Windows of
 // several adjacent cells share a tile when they lie within 256 rows of each
 // other (the adjacent cells of a query cell come in ascending position order).
-struct TileDesc {
-    uint32_t item, tile, flags, pad;
+struct alignas(16) TileDesc {
+    uint32_t item, tile, flags, aseq;   // aseq: the producer's item sequence number (A buffer aseq & 1)
     uint32_t qbeg, qlen, qa, r0;
     uint32_t p2, p3, pad2, pad3;
     uint32_t mask[8];
@@ -173,7 +175,8 @@ __device__ __forceinline__ bool tc_exact(const double *__restrict__ X, int64_t n
 // exact pairs into the staging half (or count them).  Called by all 32 lanes.
 __device__ __noinline__ void tc_flush_survivors(const TcLaunch *__restrict__ T, const uint32_t *sq,
                                                 const uint32_t *sc, uint32_t n, gj_pair *stg, uint32_t *cnt,
-                                                uint32_t *flush_req, unsigned long long *counted, uint32_t job)
+                                                uint32_t *flush_req, unsigned long long *counted, uint32_t job,
+                                                unsigned long long *dpos = nullptr)
 {
     const int lane = threadIdx.x & 31;
     const double *__restrict__ X = T->J.ix.X;
@@ -193,7 +196,7 @@ __device__ __noinline__ void tc_flush_survivors(const TcLaunch *__restrict__ T, 
             keep = tc_exact(X, npad, d, e2bits, qpos, cpos);
         }
         const uint32_t np = keep ? ((qpos != cpos) ? 2u : 1u) : 0u;
-        if (stg == nullptr && jp == nullptr) {
+        if (stg == nullptr && jp == nullptr && dpos == nullptr) {
             *counted += np;
             continue;
         }
@@ -217,6 +220,22 @@ __device__ __noinline__ void tc_flush_survivors(const TcLaunch *__restrict__ T, 
                     jp->out[o64] = gj_pair{a, b};
                 if (np == 2 && o64 + 1 < jp->cap)
                     jp->out[o64 + 1] = gj_pair{b, a};
+            }
+            continue;
+        }
+        if (dpos) {
+            // direct output: one reservation per warp; pairs past the
+            // capacity are counted (the reservation), not written
+            unsigned long long o64 = 0;
+            if (lane == 0 && tot)
+                o64 = atomicAdd(dpos, (unsigned long long)tot);
+            o64 = __shfl_sync(0xffffffffu, o64, 0) + incl - np;
+            if (np) {
+                const uint32_t a = T->J.ix.orig[qpos], b = T->J.ix.orig[cpos];
+                if (o64 < T->J.cap)
+                    T->J.out[o64] = gj_pair{a, b};
+                if (np == 2 && o64 + 1 < T->J.cap)
+                    T->J.out[o64 + 1] = gj_pair{b, a};
             }
             continue;
         }
@@ -260,7 +279,8 @@ __device__ __forceinline__ uint32_t tc_queue_bits(const TcLaunch *__restrict__ T
                                                uint32_t qpos, uint32_t r0,
                                                uint32_t *sq, uint32_t *sc, uint32_t nq, gj_pair *stg, uint32_t *cnt,
                                                uint32_t *flush_req, unsigned long long *surv_sh,
-                                               unsigned long long *counted_sh, uint32_t job)
+                                               unsigned long long *counted_sh, uint32_t job,
+                                               unsigned long long *dpos = nullptr)
 {
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
@@ -281,7 +301,7 @@ __device__ __forceinline__ uint32_t tc_queue_bits(const TcLaunch *__restrict__ T
         if (nq + k > (uint32_t)TC_SQ) {
             unsigned long long c = 0;
             __syncwarp();
-            tc_flush_survivors(T, sq, sc, nq, stg, cnt, flush_req, &c, job);
+            tc_flush_survivors(T, sq, sc, nq, stg, cnt, flush_req, &c, job, dpos);
             __syncwarp();
             if (c)
                 atomicAdd(counted_sh, c);   // each lane counted its own pairs
@@ -300,6 +320,13 @@ __device__ __forceinline__ uint32_t tc_queue_bits(const TcLaunch *__restrict__ T
     return nq;
 }
 
+// DIRECT = false: output through per-CTA staging committed per work item
+// (exact resume; result batches for host output).  DIRECT = true: pairs go
+// straight to the output (or a many-jobs launch's job buffers) with one
+// reservation per warp, so the epilogue needs no agreement between warps and
+// runs as two groups of four warps, one per accumulator, that work on
+// alternate tiles.
+template <bool DIRECT>
 __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -318,9 +345,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
         }
         for (int i = 0; i < 2; ++i) {
             mbar_init(&S.full_a[i], 1);
-            mbar_init(&S.empty_a[i], 1);
+            mbar_init(&S.empty_a[i], 2);   // both MMA issuers commit at the item's end
             mbar_init(&S.tmem_full[i], 1);
-            mbar_init(&S.tmem_empty[i], 8);
+            mbar_init(&S.tmem_empty[i], DIRECT ? 4 : 8);   // the warps that read the accumulator
             mbar_init(&S.desc_full[i], 1);
             mbar_init(&S.epi_bar[i], 8);
         }
@@ -384,6 +411,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
                 break;
             const Item it = L.ix.items[item];
             const uint32_t qa = it.qbeg & ~7u;
+            const uint32_t aseq = nitem;
             const uint32_t abuf = nitem & 1u;
             if (lane == 0) {
                 if (!mbar_wait(&S.empty_a[abuf], ((nitem >> 1) & 1u) ^ 1u, abort, TC_LIMIT_NS)) {
@@ -436,7 +464,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
                             if (!push(pend, true))
                                 dead = true;
                         }
-                        pend = TileDesc{item, tile_idx, 0u, 0u, it.qbeg, it.qlen, qa, cr0, job, jtb, 0u, 0u};
+                        pend = TileDesc{item, tile_idx, 0u, aseq, it.qbeg, it.qlen, qa, cr0, job, jtb, 0u, 0u};
                         uint32_t nv = 0;
                         if (full) {
 #pragma unroll
@@ -527,6 +555,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
             if (lane == 0 && !trunc && !dead)
                 close_tile(false);
             if (lane == 0 && !dead) {
+                const bool single = first;   // no turn pushed yet: the item ends with its only turn
                 if (have && !trunc) {
                     pend.flags |= F_LAST | (first ? F_FIRST : 0u);
                     if (!push(pend, true))
@@ -534,8 +563,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
                 } else {
                     TileDesc M{item, first ? resume : 0u, F_MARKER | F_LAST | (first ? F_FIRST : 0u) |
                                                          (trunc ? F_TRUNC : 0u),
-                               0u, it.qbeg, it.qlen, qa, 0u, job, jtb, 0u, 0u};
+                               aseq, it.qbeg, it.qlen, qa, 0u, job, jtb, 0u, 0u};
                     if (!push(M, false))
+                        dead = true;
+                }
+                if (single && !dead) {
+                    TileDesc P{item, 0u, F_MARKER | F_PAD, aseq, it.qbeg, it.qlen, qa, 0u, job, jtb, 0u, 0u};
+                    if (!push(P, false))
                         dead = true;
                 }
             }
@@ -545,9 +579,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
                 break;
         }
         if (lane == 0) {
-            if (!dead) {
+            // one terminator per accumulator parity: each MMA issuer, and in
+            // the direct form each epilogue group, stops at its own
+            for (int t = 0; t < 2 && !dead; ++t) {
                 TileDesc Tm{};
                 Tm.flags = F_TERM;
+                Tm.aseq = nitem;   // every item before this one is finished
                 if (!push(Tm, false))
                     dead = true;
             }
@@ -559,9 +596,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
                 atomicAdd(&L.ctl->evaluated, slots);
         }
         __syncwarp();
-    } else if (warp == 1) {
-        // ------------------------------------------------------------ MMA issuer
+    } else if (warp == 1 || warp == 10) {
+        // ------------------------------------------------------------ MMA issuers
+        // Two issuing threads, one per accumulator: issuer j takes the turns
+        // of parity j.  A thread waiting on a barrier or committing stalls its
+        // own MMA stream, so with one issuer the tensor core idled for every
+        // wait, fence and commit; with two, one issuer's bookkeeping overlaps
+        // the other's MMAs.  Each issuer reads its own turns only (another
+        // parity's stage barrier may already be a phase or more ahead).  An A
+        // buffer is reused only after both issuers released it: when issuer
+        // j's turn belongs to item a (the producer's item sequence number), j
+        // has issued every MMA it will issue on items < a and commits their
+        // release (the empty barrier counts 2 arrivals per item).  Every item
+        // has a turn of each parity (the producer pads single-turn items), so
+        // neither issuer holds a buffer the producer waits for.
         if (lane == 0) {
+            const uint32_t j = (warp == 1) ? 0u : 1u;
             const uint32_t idesc = idesc_f16_f32(128, TC_N);
             const uint32_t lbo = 128, sbo = (uint32_t)T.Kp * 16;
             const uint32_t a0 = smem_addr(Abuf), b0 = smem_addr(Bbuf);
@@ -569,57 +619,71 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
             // descriptors of buffer 0 / stage 0; an operand at byte offset o adds
             // o >> 4 to the start-address field (shared addresses stay < 2^18)
             const uint64_t adesc0 = desc_kmajor(a0, lbo, sbo), bdesc0 = desc_kmajor(b0, lbo, sbo);
-            uint32_t seq = 0, turn = 0, nitem = 0, abuf = 0;
+            uint32_t a_seen = 0xffffffffu;   // item whose A load this thread has seen land
+            uint32_t next_rel = 0;           // first item this thread has not released
             bool dead = false;
-            for (;;) {
+            // the A tile of item a has landed (its buffer is not reloaded before
+            // this thread released it, so the parity cannot alias)
+            auto wait_a = [&](uint32_t a) -> bool {
+                if (a_seen == a)
+                    return true;
+                if (!mbar_wait(&S.full_a[a & 1u], (a >> 1) & 1u, abort, TC_LIMIT_NS))
+                    return false;
+                a_seen = a;
+                return true;
+            };
+            for (uint32_t seq = j;; seq += 2) {
                 const uint32_t stage = seq % (uint32_t)NS;
                 if (!mbar_wait(&S.full_b[stage], (seq / NS) & 1u, abort, TC_LIMIT_NS)) {
                     dead = true;
                     break;
                 }
-                const TileDesc D = S.ring[seq % TC_DR];
-                const uint32_t acc = turn & 1u;
-                if (!mbar_wait(&S.tmem_empty[acc], ((turn >> 1) & 1u) ^ 1u, abort, TC_LIMIT_NS)) {
-                    dead = true;
-                    break;
-                }
-                TileDesc Dm = D;
-                if (*(volatile uint32_t *)&S.flush_req)
-                    Dm.flags |= F_FLUSH;
-                S.tdesc[acc] = Dm;
-                if (D.flags & F_FIRST) {
-                    abuf = nitem & 1u;
-                    if (!mbar_wait(&S.full_a[abuf], (nitem >> 1) & 1u, abort, TC_LIMIT_NS)) {
+                const TileDesc *R = &S.ring[seq % TC_DR];
+                const uint32_t flags = R->flags;
+                const uint32_t aseq = R->aseq;
+                // release the A buffers of the items before this turn's
+                while (next_rel < aseq) {
+                    // (an item whose turns here were markers issued no MMA that
+                    // waited for its load: wait before releasing the buffer)
+                    if (!wait_a(next_rel)) {
                         dead = true;
                         break;
                     }
-                    ++nitem;
+                    mma_commit(&S.empty_a[next_rel & 1u]);
+                    ++next_rel;
                 }
-                if (!(D.flags & (F_MARKER | F_TERM))) {
-                    tc_fence_after();
-                    const uint64_t ad = adesc0 + ((abuf * T.a_bytes) >> 4);
-                    const uint64_t bd = bdesc0 + ((stage * T.b_bytes) >> 4);
-                    {
-                        const uint32_t dcol = tmem + acc * 256u;
-                        mma_f16(dcol, ad, bd, idesc, 0u);
-                        for (int ks = 1; ks < ksteps; ++ks)
-                            mma_f16(dcol, ad + (uint64_t)(ks * 16), bd + (uint64_t)(ks * 16), idesc, 1u);
+                if (dead)
+                    break;
+                const uint32_t acc = j, use = seq >> 1;   // this accumulator's use count
+                if (!mbar_wait(&S.tmem_empty[acc], (use & 1u) ^ 1u, abort, TC_LIMIT_NS)) {
+                    dead = true;
+                    break;
+                }
+                TileDesc Dm = *R;
+                if (*(volatile uint32_t *)&S.flush_req)
+                    Dm.flags |= F_FLUSH;
+                S.tdesc[acc] = Dm;
+                if (!(flags & (F_MARKER | F_TERM))) {
+                    if (!wait_a(aseq)) {
+                        dead = true;
+                        break;
                     }
+                    tc_fence_after();
+                    const uint64_t ad = adesc0 + (((aseq & 1u) * T.a_bytes) >> 4);
+                    const uint64_t bd = bdesc0 + ((stage * T.b_bytes) >> 4);
+                    const uint32_t dcol = tmem + acc * 256u;
+                    mma_f16(dcol, ad, bd, idesc, 0u);
+                    for (int ks = 1; ks < ksteps; ++ks)
+                        mma_f16(dcol, ad + (uint64_t)(ks * 16), bd + (uint64_t)(ks * 16), idesc, 1u);
                     mma_commit(&S.empty_b[stage]);
-                    if (D.flags & F_LAST)
-                        mma_commit(&S.empty_a[abuf]);
                     mbar_arrive(&S.desc_full[acc]);
                     mma_commit(&S.tmem_full[acc]);
                 } else {
                     mbar_arrive(&S.empty_b[stage]);
-                    if (D.flags & F_LAST)
-                        mma_commit(&S.empty_a[abuf]);
                     mbar_arrive(&S.desc_full[acc]);
                     mbar_arrive(&S.tmem_full[acc]);
                 }
-                ++seq;
-                ++turn;
-                if (D.flags & F_TERM)
+                if (flags & F_TERM)
                     break;
             }
             if (dead) {
@@ -628,8 +692,131 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
             }
         }
         __syncwarp();
+    } else if constexpr (DIRECT) {
+        // ------------------------------------------------------------ epilogue (direct output)
+        // Group g (warps 2-5: g = 0, warps 6-9: g = 1) takes the turns of
+        // parity g from accumulator g; each warp reads its 32 rows (its TMEM
+        // lane quadrant) across all 256 columns.  While one group scans its
+        // tile the other waits for, or scans, the next: two tiles are in the
+        // epilogue at once.
+        const int e = warp - 2, q = warp & 3;
+        const uint32_t g = (uint32_t)(e >> 2);
+        uint32_t *const sq = S.sq[e], *const sc = S.sc[e];
+        uint32_t nq = 0;
+        const float Tf0 = __int_as_float(T.Tbits);
+        uint32_t cur_aseq = 0xffffffffu;     // item whose values are cached
+        uint32_t it_qpos = 0;                // this lane's query row
+        uint32_t it_job = 0xffffffffu;       // the job of the queued survivors (none yet)
+        bool it_rvalid = false;
+        float it_Tf = Tf0;
+        unsigned long long *const dpos = (!T.jobs && !count_only) ? &L.ctl->pos : nullptr;
+        unsigned long long counted = 0;
+        bool dead = false;
+        long long t_job = clock64();
+        const bool lead = (e & 3) == 0 && lane == 0;   // one lane per group (tuning launches)
+        auto flush = [&]() {
+            unsigned long long c = 0;
+            __syncwarp();
+            tc_flush_survivors(&T, sq, sc, nq, nullptr, nullptr, nullptr, &c, it_job, dpos);
+            __syncwarp();
+            counted += c;
+            nq = 0;
+        };
+        for (uint32_t use = 0;; ++use) {
+            const uint32_t par = use & 1u;
+            if (!mbar_wait(&S.desc_full[g], par, abort, TC_LIMIT_NS) ||
+                !mbar_wait(&S.tmem_full[g], par, abort, TC_LIMIT_NS)) {
+                dead = true;
+                break;
+            }
+            tc_fence_after();
+            const TileDesc *Dp = &S.tdesc[g];
+            const uint32_t flags = Dp->flags;
+            if (flags & F_TERM)
+                break;
+            const uint32_t aseq = Dp->aseq;
+            uint32_t new_job = it_job;
+            if (aseq != cur_aseq) {
+                // per-item values (the same in every descriptor of the item)
+                cur_aseq = aseq;
+                const uint32_t qa = Dp->qa, qb = Dp->qbeg, ql = Dp->qlen;
+                it_qpos = qa + (uint32_t)(q * 32 + lane);
+                it_rvalid = it_qpos >= qb && it_qpos < qb + ql;
+                new_job = Dp->p2;
+                it_Tf = T.jobs ? __uint_as_float(Dp->p3) : Tf0;
+            }
+            uint32_t hm[8];
+#pragma unroll
+            for (int c = 0; c < 8; ++c)
+                hm[c] = 0u;
+            bool anyhit = false;
+            uint32_t r0 = 0;
+            if (!(flags & F_MARKER)) {
+                const float Tf = it_Tf;
+                const bool rvalid = it_rvalid;
+                const uint32_t tb = tmem + ((uint32_t)(q * 32) << 16) + g * 256u;
+#pragma unroll
+                for (int rd = 0; rd < 4; ++rd) {
+                    uint32_t va[32], vb[32];
+                    float ma, mb;
+                    tmem_ld32_min(tb + rd * 64u, va, ma);
+                    tmem_ld32_min(tb + rd * 64u + 32u, vb, mb);
+                    tmem_wait_ld();
+                    const bool ha = rvalid && ma <= Tf, hb = rvalid && mb <= Tf;
+                    if (__any_sync(0xffffffffu, ha || hb)) {
+                        // valid rows of the tile: read only for a chunk with hits
+                        const uint32_t *vmp = Dp->mask + rd * 2;
+                        anyhit = true;
+                        if (ha)
+                            hm[rd * 2 + 0] = hit_mask32(va, Tf) & vmp[0];
+                        if (hb)
+                            hm[rd * 2 + 1] = hit_mask32(vb, Tf) & vmp[1];
+                    }
+                }
+                if (anyhit)
+                    r0 = Dp->r0;
+            }
+            // release the accumulator (and with it the descriptor slot)
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0)
+                mbar_arrive(&S.tmem_empty[g]);
+            if (new_job != it_job) {
+                // survivors queued for another job are rechecked with its values
+                if (nq)
+                    flush();
+                if (T.job_cycles && lead) {
+                    const long long t_now = clock64();
+                    if (it_job != 0xffffffffu)
+                        atomicAdd(&T.job_cycles[it_job], (unsigned long long)(t_now - t_job));
+                    t_job = t_now;
+                }
+                it_job = new_job;
+            }
+            if (anyhit) {
+#pragma unroll
+                for (int c = 0; c < 8; ++c)
+                    if (__any_sync(0xffffffffu, hm[c] != 0u))
+                        nq = tc_queue_bits(&T, hm[c], (uint32_t)c * 32u, it_qpos, r0, sq, sc, nq, nullptr, nullptr,
+                                           nullptr, &S.surv, &S.counted, it_job, dpos);
+            }
+            if (nq >= 32u)
+                flush();
+        }
+        if (!dead && nq)
+            flush();
+        if (T.job_cycles && lead && it_job != 0xffffffffu)
+            atomicAdd(&T.job_cycles[it_job], (unsigned long long)(clock64() - t_job));
+        for (int o = 16; o; o >>= 1)
+            counted += __shfl_xor_sync(0xffffffffu, counted, o);
+        if (lane == 0 && counted)
+            atomicAdd(&S.counted, counted);
+        if (dead) {
+            S.abort = 1;
+            atomicOr(&L.ctl->err, kErrTimeout);
+        }
     } else {
-        // ------------------------------------------------------------ epilogue
+        // ------------------------------------------------------------ epilogue (staged output)
         const int e = warp - 2, q = warp & 3, hh = e >> 2;
         const int etid = threadIdx.x - 64;
         uint32_t turn = 0, es = 0, commit_tile = 0;
@@ -642,6 +829,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
         if (etid == 0)
             S.t_item = clock64();
         const float Tf0 = __int_as_float(T.Tbits);
+        uint32_t it_qpos = 0, it_job = 0;   // per-item: this lane's query row, its job
+        bool it_rvalid = false;              // the row belongs to the item
+        float it_Tf = Tf0;                   // the item's survivor threshold
         gj_pair *stg0 = count_only ? nullptr : L.staging + (size_t)blockIdx.x * 2 * TC_STG;
         // Cross-warp agreement only where a decision is needed: at the end of
         // an item and when the MMA thread flags a flush in the descriptor (a
@@ -667,24 +857,32 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
                 break;
             }
             tc_fence_after();
-            const TileDesc D = S.tdesc[acc];
-            if (D.flags & F_FIRST) {
-                commit_tile = D.tile;
+            // the descriptor slot is reused once the accumulator is released:
+            // what is needed afterwards is read now
+            const TileDesc *Dp = &S.tdesc[acc];
+            const uint32_t flags = Dp->flags, d_tile = Dp->tile, d_item = Dp->item;
+            if (flags & F_FIRST) {
+                // per-item values, the same in every descriptor of the item
+                commit_tile = d_tile;
                 failed = false;
+                const uint32_t qa = Dp->qa, qb = Dp->qbeg, ql = Dp->qlen;
+                it_qpos = qa + (uint32_t)(q * 32 + lane);
+                it_rvalid = it_qpos >= qb && it_qpos < qb + ql;
+                it_job = Dp->p2;
+                it_Tf = T.jobs ? __uint_as_float(Dp->p3) : Tf0;
             }
-            const bool is_tile = !(D.flags & (F_MARKER | F_TERM));
-            const float Tf = T.jobs ? __uint_as_float(D.p3) : Tf0;
+            const bool is_tile = !(flags & (F_MARKER | F_TERM));
+            const float Tf = it_Tf;
+            const uint32_t qpos = it_qpos;
+            const bool rvalid = it_rvalid;
             uint32_t hm0 = 0, hm1 = 0, hm2 = 0, hm3 = 0;   // per-lane hit masks of the 4 chunks
             bool anyhit = false;
-            uint32_t qpos = 0;
+            uint32_t r0 = 0;
             if (is_tile && !failed) {
                 // valid rows of this thread's 128 columns: read only for a chunk
                 // with hits, before the accumulator (and with it the descriptor
                 // slot) is released
-                const uint32_t *vmp = S.tdesc[acc].mask + hh * 4;
-                const uint32_t row = (uint32_t)(q * 32 + lane);
-                qpos = D.qa + row;
-                const bool rvalid = qpos >= D.qbeg && qpos < D.qbeg + D.qlen;
+                const uint32_t *vmp = Dp->mask + hh * 4;
                 const uint32_t tb = tmem + ((uint32_t)(q * 32) << 16) + acc * 256u + (uint32_t)hh * 128u;
                 {
                     uint32_t va[32], vb[32];
@@ -717,6 +915,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
                     }
                 }
             }
+            if (anyhit)
+                r0 = Dp->r0;
             // A warp with few hits queues them after releasing the accumulator.
             // A warp with many (dense data) queues and rechecks them before, so
             // that its staging output is seen by the flush logic in time.
@@ -737,21 +937,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
             if (anyhit) {
                 const uint32_t cb = (uint32_t)hh * 128u;
                 if (__any_sync(0xffffffffu, hm0 != 0u))
-                    nq = tc_queue_bits(&T, hm0, cb + 0u, qpos, D.r0, sq, sc, nq, stg, &S.cnt[half],
-                                       &S.flush_req, &S.surv, &S.counted, D.p2);
+                    nq = tc_queue_bits(&T, hm0, cb + 0u, qpos, r0, sq, sc, nq, stg, &S.cnt[half],
+                                       &S.flush_req, &S.surv, &S.counted, it_job);
                 if (__any_sync(0xffffffffu, hm1 != 0u))
-                    nq = tc_queue_bits(&T, hm1, cb + 32u, qpos, D.r0, sq, sc, nq, stg, &S.cnt[half],
-                                       &S.flush_req, &S.surv, &S.counted, D.p2);
+                    nq = tc_queue_bits(&T, hm1, cb + 32u, qpos, r0, sq, sc, nq, stg, &S.cnt[half],
+                                       &S.flush_req, &S.surv, &S.counted, it_job);
                 if (__any_sync(0xffffffffu, hm2 != 0u))
-                    nq = tc_queue_bits(&T, hm2, cb + 64u, qpos, D.r0, sq, sc, nq, stg, &S.cnt[half],
-                                       &S.flush_req, &S.surv, &S.counted, D.p2);
+                    nq = tc_queue_bits(&T, hm2, cb + 64u, qpos, r0, sq, sc, nq, stg, &S.cnt[half],
+                                       &S.flush_req, &S.surv, &S.counted, it_job);
                 if (__any_sync(0xffffffffu, hm3 != 0u))
-                    nq = tc_queue_bits(&T, hm3, cb + 96u, qpos, D.r0, sq, sc, nq, stg, &S.cnt[half],
-                                       &S.flush_req, &S.surv, &S.counted, D.p2);
+                    nq = tc_queue_bits(&T, hm3, cb + 96u, qpos, r0, sq, sc, nq, stg, &S.cnt[half],
+                                       &S.flush_req, &S.surv, &S.counted, it_job);
                 if (early && nq) {
                     unsigned long long c = 0;
                     __syncwarp();
-                    tc_flush_survivors(&T, sq, sc, nq, stg, &S.cnt[half], &S.flush_req, &c, D.p2);
+                    tc_flush_survivors(&T, sq, sc, nq, stg, &S.cnt[half], &S.flush_req, &c, it_job);
                     __syncwarp();
                     if (c)
                         atomicAdd(&S.counted, c);
@@ -767,22 +967,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
             ++turn;
             // the accumulator is released; recheck queued survivors now when the
             // queue is half full, or when the item's results must be complete
-            const bool item_end = (D.flags & (F_LAST | F_MARKER)) != 0;
-            const bool flush = (D.flags & F_FLUSH) != 0;
-            if (nq >= 32u || ((item_end || flush || (D.flags & F_TERM)) && nq)) {
+            const bool item_end = (flags & F_LAST) != 0;   // (every marker but a pad ends its item)
+            const bool flush = (flags & F_FLUSH) != 0;
+            if (nq >= 32u || ((item_end || flush || (flags & F_TERM)) && nq)) {
                 unsigned long long c = 0;
                 __syncwarp();
-                tc_flush_survivors(&T, sq, sc, nq, stg, &S.cnt[half], &S.flush_req, &c, D.p2);
+                tc_flush_survivors(&T, sq, sc, nq, stg, &S.cnt[half], &S.flush_req, &c, it_job);
                 __syncwarp();
                 if (c)
                     atomicAdd(&S.counted, c);
                 nq = 0;
             }
-            if (D.flags & F_TERM)
+            if (flags & F_TERM)
                 break;
             if (T.job_cycles && item_end && etid == 0) {
                 const long long t_now = clock64();
-                atomicAdd(&T.job_cycles[L.ix.items[D.item].pad], (unsigned long long)(t_now - S.t_item));
+                atomicAdd(&T.job_cycles[L.ix.items[d_item].pad], (unsigned long long)(t_now - S.t_item));
                 S.t_item = t_now;
             }
             if (count_only)
@@ -794,7 +994,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
                 break;
             }
             const uint32_t cnt = S.cnt[half];
-            const bool commit = !failed && !(D.flags & F_TRUNC);
+            const bool commit = !failed && !(flags & F_TRUNC);
             if (etid == 0) {
                 uint32_t ok = 0;
                 unsigned long long b = 0;
@@ -812,7 +1012,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
                 if (item_end && !(commit && ok)) {
                     uint32_t slot = atomicAdd(&L.ctl->dout_n, 1u);
                     if (slot < L.dout_cap)
-                        L.dout[slot] = Deferred{D.item, commit_tile};
+                        L.dout[slot] = Deferred{d_item, commit_tile};
                     else
                         atomicOr(&L.ctl->err, kErrDeferred);
                 }
@@ -832,7 +1032,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
                     for (uint32_t i = (uint32_t)etid; i < cnt; i += 256u)
                         L.out[b + i] = stg[i];
                     if (!item_end && is_tile)
-                        commit_tile = D.tile + 1;
+                        commit_tile = d_tile + 1;
                 } else {
                     failed = true;
                 }
@@ -1078,7 +1278,7 @@ cudaError_t tc_jobs_launch_attr(int Kp)
     size_t sm = 0;
     if (tc_stages(Kp, &a, &b, &ob, &os, &sm) < 2)
         return cudaErrorInvalidValue;
-    return cudaFuncSetAttribute(k_join_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    return cudaFuncSetAttribute(k_join_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
 }
 
 // (call tc_jobs_launch_attr first: this launcher sets no attribute, so it can
@@ -1099,11 +1299,11 @@ cudaError_t launch_join_tc_jobs(const JoinLaunch &L, const void *XA, const void 
     T.NS = tc_stages(T.Kp, &T.a_bytes, &T.b_bytes, &T.off_b, &T.off_s, &sm);
     if (T.NS < 2)
         return cudaErrorInvalidValue;
-    k_join_tc<<<grid, TC_THREADS, sm, s>>>(T);
+    k_join_tc<true><<<grid, TC_THREADS, sm, s>>>(T);   // every job writes its own buffer directly
     return cudaGetLastError();
 }
 
-cudaError_t launch_join_tc(const gj_index *h, const JoinLaunch &L, int grid, cudaStream_t s)
+cudaError_t launch_join_tc(const gj_index *h, const JoinLaunch &L, int grid, cudaStream_t s, bool direct)
 {
     TcLaunch T{};
     T.J = L;
@@ -1115,11 +1315,15 @@ cudaError_t launch_join_tc(const gj_index *h, const JoinLaunch &L, int grid, cud
     T.NS = tc_stages(T.Kp, &T.a_bytes, &T.b_bytes, &T.off_b, &T.off_s, &sm);
     if (T.NS < 2)
         return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(k_join_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = direct ? cudaFuncSetAttribute(k_join_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)
+                           : cudaFuncSetAttribute(k_join_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess)
         return e;
     note_launch();
-    k_join_tc<<<grid, TC_THREADS, sm, s>>>(T);
+    if (direct)
+        k_join_tc<true><<<grid, TC_THREADS, sm, s>>>(T);
+    else
+        k_join_tc<false><<<grid, TC_THREADS, sm, s>>>(T);
     return cudaGetLastError();
 }
 
