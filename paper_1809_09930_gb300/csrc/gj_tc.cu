@@ -82,6 +82,7 @@ struct TcShared {
     uint64_t full_a[2], empty_a[2];
     uint64_t tmem_full[2], tmem_empty[2], desc_full[2];
     uint64_t epi_bar[2];
+    uint64_t fin[2];         // per MMA issuer: its last commit has landed
     TileDesc ring[TC_DR];
     TileDesc tdesc[2];
     uint32_t tmem_base;
@@ -350,6 +351,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
             mbar_init(&S.tmem_empty[i], DIRECT ? 4 : 8);   // the warps that read the accumulator
             mbar_init(&S.desc_full[i], 1);
             mbar_init(&S.epi_bar[i], 8);
+            mbar_init(&S.fin[i], 1);
         }
         S.abort = 0;
         S.flush_req = 0;
@@ -484,22 +486,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
                 }
                 ++tile_idx;
             };
-            auto pack_window = [&](int64_t s0, const int64_t e0) {   // lane 0 only
+            // Pack rows [s0, e0) of one window into partial tiles.  Returns e0,
+            // or the start of a run of whole tiles (no tile open, s0 a multiple
+            // of 8, at least TC_N rows left), which the warp pushes together.
+            auto pack_window = [&](int64_t s0, const int64_t e0) -> int64_t {   // lane 0 only
                 while (s0 < e0 && !trunc && !dead) {
-                    // whole tiles of a long window: every row valid
-                    if (!open && (s0 & 7) == 0 && e0 - s0 >= TC_N) {
-                        cr0 = (uint32_t)s0;
-                        open = true;
-                        close_tile(true);
-                        s0 += TC_N;
-                        continue;
-                    }
+                    if (!open && (s0 & 7) == 0 && e0 - s0 >= TC_N)
+                        return s0;
                     // (windows come in ascending order; one that does not
                     // starts a tile of its own)
                     if (open && (s0 >= (int64_t)cr0 + TC_N || s0 < (int64_t)cr0))
                         close_tile(false);
                     if (trunc || dead)
-                        return;
+                        return e0;
                     if (!open) {
                         open = true;
                         cr0 = (uint32_t)(s0 & ~(int64_t)7);
@@ -519,6 +518,77 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
                     s0 = hi;
                     if (s0 < e0)
                         close_tile(false);   // the window runs on past this tile
+                }
+                return e0;
+            };
+            // A run of F whole tiles from row s0 (every row valid), warp-wide:
+            // the pending tile goes first (lane 0), then the run's tiles but
+            // its last, one per lane, in batches of at most NS turns (distinct
+            // stages: no lane waits for a phase another lane's turn must pass);
+            // the run's last tile becomes the pending one (its end flags are
+            // known only when the item ends).
+            auto push_run = [&](const int64_t r_s0, const uint32_t F) {
+                const uint32_t ti0 = __shfl_sync(0xffffffffu, tile_idx, 0);
+                const uint32_t skip = resume > ti0 ? min(F, resume - ti0) : 0u;   // tiles already committed
+                if (lane == 0) {
+                    tile_idx = ti0 + F;
+                    // another CTA filled the output: stop (tiles made meanwhile
+                    // are discarded by the failed commit)
+                    if (!count_only && *(volatile unsigned int *)&L.ctl->full)
+                        trunc = true;
+                    else if (skip < F && have) {
+                        if (first)
+                            pend.flags |= F_FIRST;
+                        first = false;
+                        if (!push(pend, true))
+                            dead = true;
+                        have = false;
+                    }
+                }
+                if (__shfl_sync(0xffffffffu, (trunc || dead) ? 1 : 0, 0) || skip == F)
+                    return;
+                const uint32_t sq0 = __shfl_sync(0xffffffffu, seq, 0);
+                const bool fs = __shfl_sync(0xffffffffu, first ? 1 : 0, 0) != 0;
+                const uint32_t m = F - skip - 1;   // pushed now
+                bool bad = false;
+                for (uint32_t b = 0; b < m; b += (uint32_t)NS) {
+                    const uint32_t cnt = min((uint32_t)NS, m - b);
+                    if ((uint32_t)lane < cnt) {
+                        const uint32_t i = skip + b + (uint32_t)lane, t = sq0 + b + (uint32_t)lane;
+                        const uint32_t st = t % (uint32_t)NS;
+                        if (!mbar_wait(&S.empty_b[st], ((t / NS) & 1u) ^ 1u, abort, TC_LIMIT_NS)) {
+                            bad = true;
+                        } else {
+                            const uint32_t r0 = (uint32_t)r_s0 + i * (uint32_t)TC_N;
+                            uint4 *dst = reinterpret_cast<uint4 *>(&S.ring[t % TC_DR]);
+                            dst[0] = make_uint4(item, ti0 + i, (fs && b + lane == 0) ? F_FIRST : 0u, aseq);
+                            dst[1] = make_uint4(it.qbeg, it.qlen, qa, r0);
+                            dst[2] = make_uint4(job, jtb, 0u, 0u);
+                            dst[3] = make_uint4(0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu);
+                            dst[4] = dst[3];
+                            mbar_arrive_expect_tx(&S.full_b[st], T.b_bytes);
+                            bulk_g2s(Bbuf + (size_t)st * T.b_bytes, T.XB + (size_t)r0 * T.Kp * 2, T.b_bytes,
+                                     &S.full_b[st]);
+                        }
+                    }
+                    if (__any_sync(0xffffffffu, bad)) {
+                        bad = true;
+                        break;
+                    }
+                }
+                if (lane == 0) {
+                    if (bad)
+                        dead = true;
+                    seq = sq0 + m;
+                    if (m)
+                        first = false;
+                    pend = TileDesc{item, ti0 + F - 1, 0u, aseq, it.qbeg, it.qlen, qa,
+                                    (uint32_t)r_s0 + (F - 1) * (uint32_t)TC_N, job, jtb, 0u, 0u};
+#pragma unroll
+                    for (int w = 0; w < 8; ++w)
+                        pend.mask[w] = 0xffffffffu;
+                    have = true;
+                    slots += (unsigned long long)it.qlen * TC_N * (m + 1);
                 }
             };
             for (int64_t nb0 = nb_begin; nb0 < nb_end; nb0 += 32) {
@@ -541,14 +611,33 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
                 S.win[lane][0] = ws;
                 S.win[lane][1] = we;
                 __syncwarp();
-                if (lane == 0) {
-                    const int nw = (int)min((int64_t)32, nb_end - nb0);
-                    for (int w = 0; w < nw && !trunc && !dead; ++w)
-                        pack_window(S.win[w][0], S.win[w][1]);
+                const int nw = (int)min((int64_t)32, nb_end - nb0);
+                for (int w = 0; w < nw; ++w) {
+                    const int64_t e0 = S.win[w][1];
+                    int64_t s0 = S.win[w][0];
+                    for (;;) {
+                        int64_t stop = e0;
+                        if (lane == 0)
+                            stop = pack_window(s0, e0);
+                        stop = __shfl_sync(0xffffffffu, stop, 0);
+                        trunc = __shfl_sync(0xffffffffu, trunc, 0);
+                        dead = __shfl_sync(0xffffffffu, dead, 0);
+                        if (trunc || dead || stop >= e0)
+                            break;
+                        const uint32_t F = (uint32_t)((e0 - stop) / TC_N);
+                        push_run(stop, F);
+                        trunc = __shfl_sync(0xffffffffu, trunc, 0);
+                        dead = __shfl_sync(0xffffffffu, dead, 0);
+                        if (trunc || dead)
+                            break;
+                        s0 = stop + (int64_t)F * TC_N;
+                        if (s0 >= e0)
+                            break;
+                    }
+                    if (trunc || dead)
+                        break;
                 }
                 __syncwarp();
-                trunc = __shfl_sync(0xffffffffu, trunc, 0);
-                dead = __shfl_sync(0xffffffffu, dead, 0);
                 if (trunc || dead)
                     break;
             }
@@ -641,7 +730,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
                 const TileDesc *R = &S.ring[seq % TC_DR];
                 const uint32_t flags = R->flags;
                 const uint32_t aseq = R->aseq;
-                // release the A buffers of the items before this turn's
+                // release the A buffers of the items before this turn's (at a
+                // terminator no item follows: only wait for their loads)
                 while (next_rel < aseq) {
                     // (an item whose turns here were markers issued no MMA that
                     // waited for its load: wait before releasing the buffer)
@@ -649,7 +739,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
                         dead = true;
                         break;
                     }
-                    mma_commit(&S.empty_a[next_rel & 1u]);
+                    if (!(flags & F_TERM))
+                        mma_commit(&S.empty_a[next_rel & 1u]);
                     ++next_rel;
                 }
                 if (dead)
@@ -685,6 +776,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
                 }
                 if (flags & F_TERM)
                     break;
+            }
+            // A commit's arrival lands asynchronously, after the MMAs before it
+            // complete; one still in flight when the CTA exits could land in
+            // the shared memory of the next CTA on this SM.  Commit once more
+            // and wait: the earlier arrivals of this thread have then landed.
+            if (!dead) {
+                mma_commit(&S.fin[j]);
+                if (!mbar_wait(&S.fin[j], 0u, abort, TC_LIMIT_NS))
+                    dead = true;
             }
             if (dead) {
                 S.abort = 1;
