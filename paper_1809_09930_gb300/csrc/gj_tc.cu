@@ -57,7 +57,7 @@ using namespace sm100;
 constexpr int TC_THREADS = 352;
 constexpr int TC_N = 256;        // candidate rows per tile (one M=128 x N=256 MMA per K step)
 constexpr int TC_M = 128;        // query rows per A tile
-constexpr int TC_DR = 16;        // descriptor ring entries
+constexpr int TC_MAXS = 8;       // most B-tile stages (one descriptor slot per stage)
 constexpr uint32_t TC_STG = 1u << 18;   // staging pairs per half per CTA (4 tiles of worst-case output)
 constexpr uint64_t TC_LIMIT_NS = 4000000000ull;   // 4 s per wait
 constexpr int TC_SQ = 64;        // survivor queue per epilogue warp
@@ -83,7 +83,10 @@ struct TcShared {
     uint64_t tmem_full[2], tmem_empty[2], desc_full[2];
     uint64_t epi_bar[2];
     uint64_t fin[2];         // per MMA issuer: its last commit has landed
-    TileDesc ring[TC_DR];
+    // the descriptor of a stage's current turn: the MMA issuer copies it
+    // before the stage is released (by the MMA's commit, or a marker's
+    // arrival), so the producer rewrites it only after the stage is free
+    TileDesc ring[TC_MAXS];
     TileDesc tdesc[2];
     uint32_t tmem_base;
     uint32_t abort;
@@ -381,7 +384,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
             const uint32_t stage = seq % (uint32_t)NS;
             if (!mbar_wait(&S.empty_b[stage], ((seq / NS) & 1u) ^ 1u, abort, TC_LIMIT_NS))
                 return false;
-            S.ring[seq % TC_DR] = D;
+            S.ring[stage] = D;
             if (tile) {
                 mbar_arrive_expect_tx(&S.full_b[stage], T.b_bytes);
                 bulk_g2s(Bbuf + (size_t)stage * T.b_bytes, T.XB + (size_t)D.r0 * T.Kp * 2, T.b_bytes,
@@ -550,32 +553,41 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
                 const uint32_t sq0 = __shfl_sync(0xffffffffu, seq, 0);
                 const bool fs = __shfl_sync(0xffffffffu, first ? 1 : 0, 0) != 0;
                 const uint32_t m = F - skip - 1;   // pushed now
+                // lane L pushes the run's tiles L, L + NS, ... : turns of one
+                // stage, each as soon as the stage is free (a non-blocking
+                // test per round, so the warp stays converged)
                 bool bad = false;
-                for (uint32_t b = 0; b < m; b += (uint32_t)NS) {
-                    const uint32_t cnt = min((uint32_t)NS, m - b);
-                    if ((uint32_t)lane < cnt) {
-                        const uint32_t i = skip + b + (uint32_t)lane, t = sq0 + b + (uint32_t)lane;
-                        const uint32_t st = t % (uint32_t)NS;
-                        if (!mbar_wait(&S.empty_b[st], ((t / NS) & 1u) ^ 1u, abort, TC_LIMIT_NS)) {
-                            bad = true;
-                        } else {
+                uint32_t kk = (uint32_t)lane;
+                const uint32_t st = (sq0 + (uint32_t)lane) % (uint32_t)NS;
+                const uint64_t t_start = globaltimer();
+                uint32_t rounds = 0;
+                while (__any_sync(0xffffffffu, kk < m && lane < NS)) {
+                    if (kk < m && lane < NS) {
+                        const uint32_t t = sq0 + kk;
+                        if (mbar_test(&S.empty_b[st], ((t / NS) & 1u) ^ 1u)) {
+                            const uint32_t i = skip + kk;
                             const uint32_t r0 = (uint32_t)r_s0 + i * (uint32_t)TC_N;
-                            uint4 *dst = reinterpret_cast<uint4 *>(&S.ring[t % TC_DR]);
-                            dst[0] = make_uint4(item, ti0 + i, (fs && b + lane == 0) ? F_FIRST : 0u, aseq);
+                            uint4 *dst = reinterpret_cast<uint4 *>(&S.ring[st]);
+                            dst[0] = make_uint4(item, ti0 + i, (fs && kk == 0) ? F_FIRST : 0u, aseq);
                             dst[1] = make_uint4(it.qbeg, it.qlen, qa, r0);
                             dst[2] = make_uint4(job, jtb, 0u, 0u);
                             dst[3] = make_uint4(0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu);
-                            dst[4] = dst[3];
+                            dst[4] = make_uint4(0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu);
                             mbar_arrive_expect_tx(&S.full_b[st], T.b_bytes);
                             bulk_g2s(Bbuf + (size_t)st * T.b_bytes, T.XB + (size_t)r0 * T.Kp * 2, T.b_bytes,
                                      &S.full_b[st]);
+                            kk += (uint32_t)NS;
                         }
                     }
-                    if (__any_sync(0xffffffffu, bad)) {
+                    // bounded like every other wait: the clock and the abort
+                    // flag are read every 256 rounds
+                    if ((++rounds & 255u) == 0 &&
+                        (*abort || globaltimer() - t_start > TC_LIMIT_NS)) {
                         bad = true;
                         break;
                     }
                 }
+                bad = __any_sync(0xffffffffu, bad);
                 if (lane == 0) {
                     if (bad)
                         dead = true;
@@ -727,7 +739,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
                     dead = true;
                     break;
                 }
-                const TileDesc *R = &S.ring[seq % TC_DR];
+                const TileDesc *R = &S.ring[stage];
                 const uint32_t flags = R->flags;
                 const uint32_t aseq = R->aseq;
                 // release the A buffers of the items before this turn's (at a
