@@ -54,13 +54,14 @@ namespace gj {
 
 using namespace sm100;
 
-constexpr int TC_THREADS = 352;
+constexpr int TC_THREADS = 384;   // producer, MMA issuer x2, epilogue x8, recheck
 constexpr int TC_N = 256;        // candidate rows per tile (one M=128 x N=256 MMA per K step)
 constexpr int TC_M = 128;        // query rows per A tile
 constexpr int TC_MAXS = 8;       // most B-tile stages (one descriptor slot per stage)
 constexpr uint32_t TC_STG = 1u << 18;   // staging pairs per half per CTA (4 tiles of worst-case output)
 constexpr uint64_t TC_LIMIT_NS = 4000000000ull;   // 4 s per wait
 constexpr int TC_SQ = 64;        // survivor queue per epilogue warp
+constexpr int TC_RQ = 64;        // direct form: survivors handed to the recheck warp, per epilogue warp
 
 // F_PAD: a no-op turn after an item that made one turn only, so that every
 // item has a turn of each parity (each MMA issuer sees every item)
@@ -98,6 +99,12 @@ struct TcShared {
     unsigned long long base;
     uint32_t sq[8][TC_SQ];   // per epilogue warp: survivors waiting for the FP64 recheck
     uint32_t sc[8][TC_SQ];
+    // direct form: per epilogue warp, a ring of survivors (query position,
+    // candidate position, job) that the recheck warp takes; one writer, one
+    // reader, positions counted from 0 (tail: written, head: taken)
+    uint32_t rq_q[8][TC_RQ], rq_c[8][TC_RQ], rq_j[8][TC_RQ];
+    uint32_t rq_tail[8], rq_head[8];
+    uint32_t epi_done;       // epilogue warps that finished
     unsigned long long surv;     // survivors (statistics)
     unsigned long long counted;  // pairs counted (count-only launches)
     long long t_item;            // tuning launches: clock of the last item end
@@ -282,7 +289,7 @@ __device__ __forceinline__ uint32_t hit_mask32(const uint32_t (&v)[32], float Tf
 __device__ __forceinline__ uint32_t tc_queue_bits(const TcLaunch *__restrict__ T, uint32_t mask, uint32_t col0,
                                                uint32_t qpos, uint32_t r0,
                                                uint32_t *sq, uint32_t *sc, uint32_t nq, gj_pair *stg, uint32_t *cnt,
-                                               uint32_t *flush_req, unsigned long long *surv_sh,
+                                               uint32_t *flush_req, uint32_t &surv,
                                                unsigned long long *counted_sh, uint32_t job,
                                                unsigned long long *dpos = nullptr)
 {
@@ -319,8 +326,8 @@ __device__ __forceinline__ uint32_t tc_queue_bits(const TcLaunch *__restrict__ T
         nq += k;
         found += k;
     }
-    if (lane == 0 && found)
-        atomicAdd(surv_sh, (unsigned long long)found);
+    if (lane == 0)
+        surv += found;   // (summed into the launch statistics once, at the warp's exit)
     return nq;
 }
 
@@ -358,6 +365,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
         }
         S.abort = 0;
         S.flush_req = 0;
+        for (int w = 0; w < 8; ++w)
+            S.rq_tail[w] = S.rq_head[w] = 0;
+        S.epi_done = 0;
         S.half = 0;
         S.cnt[0] = S.cnt[1] = 0;
         S.surv = 0;
@@ -804,6 +814,61 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
             }
         }
         __syncwarp();
+    } else if (warp == 11) {
+        // ------------------------------------------------------------ recheck (direct form)
+        // Takes the survivors the epilogue warps queue in their rings, 32 at a
+        // time, runs the exact FP64 test and emits the pairs: the epilogue
+        // warps go back to the accumulators without waiting for memory.  A
+        // warp whose ring is full (dense data) rechecks its survivors itself.
+        if constexpr (DIRECT) {
+            unsigned long long *const dpos = (!T.jobs && !count_only) ? &L.ctl->pos : nullptr;
+            uint32_t head[8];
+#pragma unroll
+            for (int w = 0; w < 8; ++w)
+                head[w] = 0;
+            unsigned long long counted = 0;
+            bool last = false;
+            for (;;) {
+                // every epilogue warp done: one more pass takes what is left
+                if (!last && *(volatile uint32_t *)&S.epi_done == 8u)
+                    last = true;
+                bool worked = false;
+#pragma unroll
+                for (int w = 0; w < 8; ++w) {
+                    const uint32_t tail = *(volatile uint32_t *)&S.rq_tail[w];
+                    __threadfence_block();
+                    while (head[w] != tail) {
+                        const uint32_t pos = head[w] & (uint32_t)(TC_RQ - 1);
+                        uint32_t n = min(min(tail - head[w], (uint32_t)TC_RQ - pos), 32u);
+                        // a run of one job (a many-jobs launch mixes them)
+                        const uint32_t j0 = S.rq_j[w][pos];
+                        const unsigned same = __ballot_sync(0xffffffffu, (uint32_t)lane < n && S.rq_j[w][pos + lane] == j0);
+                        n = (same == 0xffffffffu) ? 32u : (uint32_t)(__ffs(~same) - 1);
+                        unsigned long long c = 0;
+                        tc_flush_survivors(&T, &S.rq_q[w][pos], &S.rq_c[w][pos], n, nullptr, nullptr, nullptr, &c, j0,
+                                           dpos);
+                        counted += c;
+                        head[w] += n;
+                        __syncwarp();
+                        if (lane == 0)
+                            *(volatile uint32_t *)&S.rq_head[w] = head[w];
+                        __syncwarp();
+                        worked = true;
+                    }
+                }
+                if (last)
+                    break;
+                if (!worked) {
+                    if (*abort)
+                        break;
+                    __nanosleep(2000);   // a ring fills in ~100 us of sparse data
+                }
+            }
+            for (int o = 16; o; o >>= 1)
+                counted += __shfl_xor_sync(0xffffffffu, counted, o);
+            if (lane == 0 && counted)
+                atomicAdd(&S.counted, counted);
+        }
     } else if constexpr (DIRECT) {
         // ------------------------------------------------------------ epilogue (direct output)
         // Group g (warps 2-5: g = 0, warps 6-9: g = 1) takes the turns of
@@ -823,6 +888,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
         float it_Tf = Tf0;
         unsigned long long *const dpos = (!T.jobs && !count_only) ? &L.ctl->pos : nullptr;
         unsigned long long counted = 0;
+        uint32_t surv_w = 0;                 // survivors this warp found (lane 0)
+        uint32_t rq_tail = 0;                // this warp's ring: positions written
         bool dead = false;
         long long t_job = clock64();
         const bool lead = (e & 3) == 0 && lane == 0;   // one lane per group (tuning launches)
@@ -893,6 +960,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
             __syncwarp();
             if (lane == 0)
                 mbar_arrive(&S.tmem_empty[g]);
+            // reconverge: otherwise lanes 1-31 run ahead into the next wait's
+            // polling loop and lane 0's remaining work interleaves with it
+            __syncwarp();
             if (new_job != it_job) {
                 // survivors queued for another job are rechecked with its values
                 if (nq)
@@ -906,17 +976,73 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
                 it_job = new_job;
             }
             if (anyhit) {
+                // this lane's survivors: marked columns with cpos >= qpos (one
+                // orientation; rows of the other searched cells lie after the
+                // query cell)
+                uint32_t k = 0;
 #pragma unroll
-                for (int c = 0; c < 8; ++c)
-                    if (__any_sync(0xffffffffu, hm[c] != 0u))
-                        nq = tc_queue_bits(&T, hm[c], (uint32_t)c * 32u, it_qpos, r0, sq, sc, nq, nullptr, nullptr,
-                                           nullptr, &S.surv, &S.counted, it_job, dpos);
+                for (int c = 0; c < 8; ++c) {
+                    const uint32_t col0 = r0 + (uint32_t)c * 32u;
+                    if (col0 + 31u < it_qpos)
+                        hm[c] = 0u;
+                    else if (col0 < it_qpos)
+                        hm[c] &= ~((1u << (it_qpos - col0)) - 1u);
+                    k += (uint32_t)__popc(hm[c]);
+                }
+                uint32_t incl = k;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o)
+                        incl += y;
+                }
+                const uint32_t tot = __shfl_sync(0xffffffffu, incl, 31);
+                if (tot) {
+                    const uint32_t rhead = *(volatile uint32_t *)&S.rq_head[e];
+                    if (rq_tail + tot - rhead <= (uint32_t)TC_RQ) {
+                        // room in the ring: hand them to the recheck warp
+                        uint32_t at = rq_tail + incl - k;
+#pragma unroll
+                        for (int c = 0; c < 8; ++c) {
+                            uint32_t mm = hm[c];
+                            while (mm) {
+                                const uint32_t b = (uint32_t)(__ffs(mm) - 1);
+                                mm &= mm - 1u;
+                                const uint32_t slot = at & (uint32_t)(TC_RQ - 1);
+                                S.rq_q[e][slot] = it_qpos;
+                                S.rq_c[e][slot] = r0 + (uint32_t)c * 32u + b;
+                                S.rq_j[e][slot] = it_job;
+                                ++at;
+                            }
+                        }
+                        __syncwarp();
+                        __threadfence_block();
+                        rq_tail += tot;
+                        if (lane == 0) {
+                            *(volatile uint32_t *)&S.rq_tail[e] = rq_tail;
+                            surv_w += tot;
+                        }
+                        __syncwarp();
+                    } else {
+                        // ring full (dense data): recheck them here
+#pragma unroll
+                        for (int c = 0; c < 8; ++c)
+                            if (__any_sync(0xffffffffu, hm[c] != 0u))
+                                nq = tc_queue_bits(&T, hm[c], (uint32_t)c * 32u, it_qpos, r0, sq, sc, nq, nullptr,
+                                                   nullptr, nullptr, surv_w, &S.counted, it_job, dpos);
+                    }
+                }
             }
             if (nq >= 32u)
                 flush();
         }
         if (!dead && nq)
             flush();
+        __syncwarp();
+        if (lane == 0) {
+            atomicAdd(&S.epi_done, 1u);
+            if (surv_w)
+                atomicAdd(&S.surv, (unsigned long long)surv_w);
+        }
         if (T.job_cycles && lead && it_job != 0xffffffffu)
             atomicAdd(&T.job_cycles[it_job], (unsigned long long)(clock64() - t_job));
         for (int o = 16; o; o >>= 1)
@@ -935,6 +1061,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
         bool failed = false, dead = false;
         uint32_t *const sq = S.sq[e], *const sc = S.sc[e];
         uint32_t nq = 0;
+        uint32_t surv_w = 0;   // survivors this warp found (lane 0)
         // tuning launches: the cycles from one item end to the next are the
         // cost of the later item in the steady state (the epilogue is the
         // pipeline's last stage); summed per job
@@ -1043,6 +1170,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
                 __syncwarp();
                 if (lane == 0)
                     mbar_arrive(&S.tmem_empty[acc]);
+                __syncwarp();
             }
             const uint32_t half = S.half;
             gj_pair *stg = stg0 ? stg0 + (size_t)half * TC_STG : nullptr;
@@ -1050,16 +1178,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
                 const uint32_t cb = (uint32_t)hh * 128u;
                 if (__any_sync(0xffffffffu, hm0 != 0u))
                     nq = tc_queue_bits(&T, hm0, cb + 0u, qpos, r0, sq, sc, nq, stg, &S.cnt[half],
-                                       &S.flush_req, &S.surv, &S.counted, it_job);
+                                       &S.flush_req, surv_w, &S.counted, it_job);
                 if (__any_sync(0xffffffffu, hm1 != 0u))
                     nq = tc_queue_bits(&T, hm1, cb + 32u, qpos, r0, sq, sc, nq, stg, &S.cnt[half],
-                                       &S.flush_req, &S.surv, &S.counted, it_job);
+                                       &S.flush_req, surv_w, &S.counted, it_job);
                 if (__any_sync(0xffffffffu, hm2 != 0u))
                     nq = tc_queue_bits(&T, hm2, cb + 64u, qpos, r0, sq, sc, nq, stg, &S.cnt[half],
-                                       &S.flush_req, &S.surv, &S.counted, it_job);
+                                       &S.flush_req, surv_w, &S.counted, it_job);
                 if (__any_sync(0xffffffffu, hm3 != 0u))
                     nq = tc_queue_bits(&T, hm3, cb + 96u, qpos, r0, sq, sc, nq, stg, &S.cnt[half],
-                                       &S.flush_req, &S.surv, &S.counted, it_job);
+                                       &S.flush_req, surv_w, &S.counted, it_job);
                 if (early && nq) {
                     unsigned long long c = 0;
                     __syncwarp();
@@ -1075,6 +1203,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
                 __syncwarp();
                 if (lane == 0)
                     mbar_arrive(&S.tmem_empty[acc]);
+                __syncwarp();
             }
             ++turn;
             // the accumulator is released; recheck queued survivors now when the
@@ -1150,11 +1279,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
                 }
             }
         }
+        if (lane == 0 && surv_w)
+            atomicAdd(&S.surv, (unsigned long long)surv_w);
         if (dead) {
             S.abort = 1;
             atomicOr(&L.ctl->err, kErrTimeout);
         }
-
     }
 
     __syncthreads();
