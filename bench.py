@@ -55,6 +55,9 @@ def parse():
     ap.add_argument("--nq", type=int, default=200_000, help="queries of the qe workload")
     ap.add_argument("--no-plain", action="store_true",
                     help="skip the one-shot plain FP64 join of the d=16 set beside the tc form")
+    ap.add_argument("--plain-full", action="store_true",
+                    help="run the plain FP64 join over the whole set at every listed d (minutes at d = 32 "
+                         "and 64) instead of timing a 1/32 part of the d = 32 and 64 sets")
     ap.add_argument("--dims", default=None, help="comma list of d for the paper-scale workload")
     ap.add_argument("--n", type=int, default=2_000_000)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
@@ -284,7 +287,7 @@ def reference_arm(args, runs):
     print(json.dumps(out), flush=True)
 
 
-def plain_leg(gj, torch, data, col, fp64_tflops, stream, tune=True):
+def plain_leg(gj, torch, data, col, fp64_tflops, stream, tune=True, full=False):
     """One plain FP64 join (SHORTC, no tensor cores) of the d=16 set, timed by
     the library's CUDA events, with its FP64-pipe roofline fraction."""
     for r, X, Xd in data:
@@ -316,9 +319,37 @@ def plain_leg(gj, torch, data, col, fp64_tflops, stream, tune=True):
                             "peak_source": "FP64 FMA probe measured in this run x 3/4 (DADD+DFMA mix)"}}
         if cnt != col["pairs"].get(16):
             out["mismatch"] = f"plain found {cnt} pairs, tc {col['pairs'].get(16)}"
-        out["sampled"] = plain_sampled(gj, data, col, stream, peak)
+        if full:
+            out["full"] = plain_full(gj, data, col, stream, peak)
+        else:
+            out["sampled"] = plain_sampled(gj, data, col, stream, peak)
         return out
     return None
+
+
+def plain_full(gj, data, col, stream, peak):
+    """The plain FP64 join of the d = 32 and 64 sets over the whole set, once
+    each, into the device buffer the tensor-core form filled: measured join
+    time, FP64 roofline fraction, equal |R|, and the join-time ratio."""
+    res = {}
+    steps = max(1, col.get("steps", 1))
+    for r, X, Xd in data:
+        if r["d"] == 16:
+            continue
+        with gj.Index(Xd, r["eps"], k=0, stream=stream.cuda_stream) as ix:
+            info = ix.info()
+            st, cnt = gj.gj_self_join(ix.h, col["out"][r["d"]])
+            if st != gj.GJ_OK:
+                raise RuntimeError(f"plain join failed: {gj.gj_status_string(st)}")
+            s = ix.stats()
+        join_s = s["join_ms"] * 1e-3
+        achieved = 3.0 * s["dims"] / join_s / 1e12
+        tc_s = col["join_ms_d"].get(r["d"], 0.0) * 1e-3 / steps
+        res[r["d"]] = {"join_s": join_s, "pairs": cnt, "k": info["k"],
+                       "same_count_as_tc": cnt == col["pairs"].get(r["d"]),
+                       "evals_per_s": info["candidate_pairs"] / join_s, "fp64_frac": achieved / peak,
+                       "tc_join_speedup": join_s / tc_s if tc_s else None}
+    return res
 
 
 def plain_sampled(gj, data, col, stream, peak, nparts=32):
@@ -677,21 +708,31 @@ def main():
         hin = [torch.from_numpy(X).pin_memory() for _, X, _ in data]
         hout = {r["d"]: torch.empty((col["cap"][r["d"]], 2), dtype=torch.int32).pin_memory()
                 for r, _, _ in data}
+        phases = {"build_s": 0.0, "join_s": 0.0, "close_s": 0.0}
+
         def e2e_step():
             ev = 0
             for (r, X, _), hx in zip(data, hin):
                 t = tuned.get(r["d"])
+                p0 = time.perf_counter()
                 ix = gj.Index(hx, r["eps"], flags=flags, batch_pairs=t["batch_pairs"] if t else 0,
                               **settings(r["d"]))
                 info = ix.info()
+                p1 = time.perf_counter()
                 st, cnt = gj.gj_self_join_part(ix.h, rank, world, hout[r["d"]])
                 if st != gj.GJ_OK:
                     raise RuntimeError(gj.gj_status_string(st))
+                p2 = time.perf_counter()
                 ev += info["candidate_pairs"]
                 ix.close()
+                phases["build_s"] += p1 - p0
+                phases["join_s"] += p2 - p1
+                phases["close_s"] += time.perf_counter() - p2
             return ev
         e2e_step()
         torch.cuda.synchronize()
+        for k in phases:
+            phases[k] = 0.0
         t0 = time.perf_counter()
         ev = 0
         for _ in range(steps):
@@ -702,13 +743,14 @@ def main():
         h2d = sum(X.nbytes for _, X, _ in data)
         d2h = sum(8 * col["pairs"][r["d"]] for r, _, _ in data)
         e2e = {"value": ev / e2e_s, "unit": "distance evals/s", "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h}
+               "d2h_bytes_per_step": d2h,
+               "ms_per_step_by_phase": {k.replace("_s", ""): 1e3 * v / steps for k, v in phases.items()}}
 
     # the plain FP64 form of the same d=16 join, once, for the TC-vs-plain ratio
     plain = None
     if args.form == "tc" and not args.no_plain and rank == 0 and world == 1:
         col["steps"] = steps
-        plain = plain_leg(gj, torch, data, col, fp64_tflops, stream, tune=not args.no_tune)
+        plain = plain_leg(gj, torch, data, col, fp64_tflops, stream, tune=not args.no_tune, full=args.plain_full)
         if plain and col["join_ms_d"].get(16):
             # same join, same exact pair set: join time of the plain form over the tc form's
             plain["tc_join_speedup"] = plain["join_s"] / (col["join_ms_d"][16] * 1e-3 / steps)

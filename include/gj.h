@@ -59,8 +59,9 @@ extern "C" {
 #define GJ_TC_FILTER  (1u << 3)  /* tensor-core candidate filter + exact FP64 recheck (no paper counterpart) */
 #define GJ_AUTOTUNE   (1u << 4)  /* build: pick k, query block, tile and b_s by timed trials (gj_autotune) */
 #define GJ_TUNE_FORM  (1u << 5)  /* autotune: also try both forms (plain and GJ_TC_FILTER), keep the faster */
-#define GJ_HOST_BATCHED (1u << 6) /* host output always through the result batches of Sec. 3.2.2,
-                                   * even where the device can address the host buffer directly */
+#define GJ_HOST_BATCHED (1u << 6) /* host output always through the result batches of Sec. 3.2.2
+                                   * (a tensor-core index otherwise fills one device buffer of cap
+                                   * pairs and copies it)                                      */
 #define GJ_DEFAULT_FLAGS (GJ_REORDER | GJ_SORTIDU | GJ_SHORTC)
 
 /* One result pair: original row indices of the two points. */
@@ -198,10 +199,12 @@ int gj_autotune(const double *points, int64_t n, int32_t d, double eps, const gj
  * are then unspecified), GJ_ERR_INVALID_ARG when pairs_out is device memory of
  * another device, or another error code.  Pageable host output is
  * copied in result batches (Sec. 3.2.2) on a second stream while the next
- * batch runs.  Pinned host memory that the device can address (cudaMallocHost,
- * cudaHostAlloc, mapped cudaHostRegister; CUDA reports a device pointer for
- * it) is written by the join kernels directly, in one pass as for device
- * memory; GJ_HOST_BATCHED in the build flags sends it through the batches.
+ * batch runs.  The kernels write device memory only: host output, pageable
+ * or pinned, is always filled by copies.  For an index built with
+ * GJ_TC_FILTER (and without GJ_HOST_BATCHED) the join runs in one pass into a
+ * device buffer of cap pairs from the stream-ordered pool, copied to
+ * pairs_out when the join ends; it falls back to the result batches when that
+ * buffer cannot be allocated.
  */
 int gj_self_join(gj_index *h, gj_pair *pairs_out, uint64_t cap, uint64_t *count);
 
@@ -232,9 +235,8 @@ int gj_self_join_part(gj_index *h, int32_t part, int32_t nparts, gj_pair *pairs_
  *              returns GJ_ERR_INVALID_ARG; NULL with cap == 0 counts only
  *   count      out: |Q join_eps E|
  * One kernel launch writes the pairs and counts them: into pairs_out directly
- * when the device can address it (device memory; pinned host memory unless
- * the index was built with GJ_HOST_BATCHED), else into a device buffer that is
- * then copied to the host.  Returns GJ_OK;
+ * when it is device memory, else into a device buffer of cap pairs that is
+ * then copied to the host buffer.  Returns GJ_OK;
  * GJ_ERR_CAPACITY when the result exceeds cap (*count holds its size; the
  * buffer holds an unspecified cap of them); GJ_ERR_NONFINITE for a NaN or
  * infinite query coordinate; or another error code.  The eps is the index's.
@@ -396,6 +398,15 @@ int gj_debug_tc_tile(const uint16_t *A, const uint16_t *B, int32_t Kp, float *D)
  *               rounded up to fp32).
  * Returns GJ_OK or GJ_ERR_INVALID_ARG. */
 int gj_tc_threshold(double eps, double sigma, double R0, int32_t d, float *T);
+
+/* Diagnostic (no paper counterpart): the limit, in nanoseconds, of every
+ * bounded device-side wait of the tensor-core joins launched after the call,
+ * process-wide (0 restores the default, 4 s per wait).  A limit of a few
+ * nanoseconds makes a join's waits run out: the kernel records the expiry,
+ * lets its copies and MMAs in flight land, frees its tensor memory and
+ * returns, and the join returns GJ_ERR_TIMEOUT with the context usable.  Used
+ * by the tests to exercise that path without any device fault.  Returns GJ_OK. */
+int gj_debug_set_wait_limit(uint64_t ns);
 
 /* Measurement helper (no paper counterpart): number of CUDA kernels this
  * library has launched in this process so far (all handles, all threads). */

@@ -45,7 +45,7 @@ void pool_keep(int device)
     cudaGetLastError();
     done.fetch_or((uint64_t)1 << device);
 }
-gj_pair *device_view(gj_pair *p, bool allow_host)
+gj_pair *device_view(gj_pair *p)
 {
     if (!p)
         return nullptr;
@@ -56,8 +56,6 @@ gj_pair *device_view(gj_pair *p, bool allow_host)
     }
     if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged)
         return p;
-    if (allow_host && a.type == cudaMemoryTypeHost && a.devicePointer)
-        return static_cast<gj_pair *>(a.devicePointer);
     return nullptr;
 }
 bool device_memory_of(const void *p, int device)
@@ -362,9 +360,11 @@ int join_impl(gj_index *h, int part, int nparts, gj_pair *pairs_out, uint64_t ca
     // pairs per CTA staging area: plain >= 4 tiles of output; tensor-core: two halves
     const uint32_t stg_cap = 1u << 16;
     const size_t stg_per_cta = h->tc_ready ? tc_staging_pairs_per_cta() : (size_t)stg_cap;
-    // device memory, or pinned host memory the kernels can write directly
-    // (one pass, no result batches); pageable host memory goes through batches
-    gj_pair *const direct = device_view(pairs_out, !(h->cfg.flags & GJ_HOST_BATCHED));
+    // The kernels write device memory only.  Host output (pageable or
+    // pinned) reaches the host by copies: through the result batches of
+    // Sec. 3.2.2, or, for a tensor-core index, from one device buffer of cap
+    // pairs filled by the direct form.
+    gj_pair *const direct = device_view(pairs_out);
     const bool dev_out = direct != nullptr;
     const bool count_only_call = (cap == 0);
 
@@ -376,6 +376,33 @@ int join_impl(gj_index *h, int part, int nparts, gj_pair *pairs_out, uint64_t ca
         if (st != GJ_OK)
             return st;
         return total > cap ? GJ_ERR_CAPACITY : GJ_OK;
+    }
+    if (h->tc_ready && !(h->cfg.flags & GJ_HOST_BATCHED)) {
+        // host output: the direct form into a device buffer of cap pairs (from
+        // the stream-ordered pool), then one copy of the pairs written; with no
+        // room for the buffer, the result batches below
+        gj_pair *dbuf = nullptr;
+        if (dev_alloc(&dbuf, (size_t)cap * sizeof(gj_pair), h->stream) == cudaSuccess) {
+            uint64_t total = 0;
+            int st = join_tc_direct(h, part, nparts, nq, grid, dbuf, cap, &total);
+            if (st == GJ_OK) {
+                const uint64_t ncopy = std::min<uint64_t>(total, cap);
+                cudaError_t e = ncopy ? cudaMemcpyAsync(pairs_out, dbuf, ncopy * sizeof(gj_pair),
+                                                        cudaMemcpyDeviceToHost, h->stream)
+                                      : cudaSuccess;
+                if (e == cudaSuccess)
+                    e = cudaStreamSynchronize(h->stream);
+                if (e != cudaSuccess)
+                    st = cuda_status(e);
+            }
+            dev_free(dbuf, h->stream);
+            *count = total;
+            h->last.total_ms = now_ms() - t_start;
+            if (st != GJ_OK)
+                return st;
+            return total > cap ? GJ_ERR_CAPACITY : GJ_OK;
+        }
+        cudaGetLastError();
     }
 
     JoinBuffers B;

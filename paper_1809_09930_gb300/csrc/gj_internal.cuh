@@ -134,10 +134,9 @@ inline void dev_free(void *p, cudaStream_t s)
         cudaFreeAsync(p, s);
 }
 void pool_keep(int device);
-// A device-addressable view of an output buffer: device or managed memory as
-// it is; pinned host memory through the device pointer CUDA reports for it
-// (when allow_host); nullptr for pageable host memory.
-gj_pair *device_view(gj_pair *p, bool allow_host);
+// An output buffer the kernels may write: device or managed memory as it is;
+// nullptr for host memory (pageable or pinned), which the join fills by copies.
+gj_pair *device_view(gj_pair *p);
 // Device memory of `device` itself, or managed memory: a buffer the kernels of
 // a handle on `device` may read and write.
 bool device_memory_of(const void *p, int device);

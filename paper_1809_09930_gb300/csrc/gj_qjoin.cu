@@ -114,7 +114,7 @@ extern "C" int gj_join_qe(gj_index *h, const double *queries, int64_t nq, gj_pai
     uint32_t *queue = nullptr;
     gj_pair *dbuf = nullptr;
     JoinCtl hctl{};
-    gj_pair *const direct = device_view(pairs_out, !(h->cfg.flags & GJ_HOST_BATCHED));
+    gj_pair *const direct = device_view(pairs_out);   // host output: a device buffer, then a copy
     const bool dev_out = direct != nullptr;
     uint64_t total = 0;
     e = cudaMalloc(&ctl, sizeof(JoinCtl));

@@ -75,17 +75,19 @@ __device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity)
 
 // Wait for the phase with the given parity, for at most `limit_ns`.  Returns
 // false on timeout or when *abort becomes non-zero.  The clock and the abort
-// flag are read every 256 polls only (reading %globaltimer is not free).
+// flag are read every 256 polls only (reading %globaltimer is not free), or
+// every poll under a limit below 1 ms (a diagnostic setting).
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile uint32_t *abort,
                                           uint64_t limit_ns)
 {
     if (mbar_try_wait(bar, parity))
         return true;
     const uint64_t t0 = globaltimer();
+    const bool fine = limit_ns < 1000000ull;
     for (uint32_t it = 1;; ++it) {
         if (mbar_try_wait(bar, parity))
             return true;
-        if ((it & 255u) == 0) {
+        if (fine || (it & 255u) == 0) {
             if (*abort)
                 return false;
             if (globaltimer() - t0 > limit_ns)

@@ -45,6 +45,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <vector>
 
 #include "gj_internal.cuh"
@@ -60,6 +61,17 @@ constexpr int TC_M = 128;        // query rows per A tile
 constexpr int TC_MAXS = 8;       // most B-tile stages (one descriptor slot per stage)
 constexpr uint32_t TC_STG = 1u << 18;   // staging pairs per half per CTA (4 tiles of worst-case output)
 constexpr uint64_t TC_LIMIT_NS = 4000000000ull;   // 4 s per wait
+
+// Diagnostic: the limit of every bounded wait in later tensor-core joins
+// (0: TC_LIMIT_NS).  A short limit makes the waits run out, which exercises
+// the timeout path (error status, copies in flight drained, TMEM freed)
+// without any fault.
+static std::atomic<unsigned long long> g_wait_limit_ns{0};
+static unsigned long long wait_limit_ns()
+{
+    const unsigned long long v = g_wait_limit_ns.load(std::memory_order_relaxed);
+    return v ? v : TC_LIMIT_NS;
+}
 constexpr int TC_SQ = 64;        // survivor queue per epilogue warp
 constexpr int TC_RQ = 64;        // direct form: survivors handed to the recheck warp, per epilogue warp
 
@@ -124,6 +136,7 @@ struct TcLaunch {
     int Tbits;
     uint32_t a_bytes, b_bytes;
     uint32_t off_b, off_s;
+    unsigned long long limit_ns;   // every bounded wait of the launch gives up after this
 };
 
 __device__ __forceinline__ int64_t tc_lower_u(const double *__restrict__ U, int64_t lo, int64_t hi, double ref,
@@ -392,7 +405,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
         unsigned long long slots = 0;   // candidate pairs of the pushed tiles (lane 0)
         auto push = [&](const TileDesc &D, bool tile) -> bool {   // lane 0 only
             const uint32_t stage = seq % (uint32_t)NS;
-            if (!mbar_wait(&S.empty_b[stage], ((seq / NS) & 1u) ^ 1u, abort, TC_LIMIT_NS))
+            if (!mbar_wait(&S.empty_b[stage], ((seq / NS) & 1u) ^ 1u, abort, T.limit_ns))
                 return false;
             S.ring[stage] = D;
             if (tile) {
@@ -429,7 +442,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
             const uint32_t aseq = nitem;
             const uint32_t abuf = nitem & 1u;
             if (lane == 0) {
-                if (!mbar_wait(&S.empty_a[abuf], ((nitem >> 1) & 1u) ^ 1u, abort, TC_LIMIT_NS)) {
+                if (!mbar_wait(&S.empty_a[abuf], ((nitem >> 1) & 1u) ^ 1u, abort, T.limit_ns)) {
                     dead = true;
                 } else {
                     mbar_arrive_expect_tx(&S.full_a[abuf], T.a_bytes);
@@ -591,8 +604,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
                     }
                     // bounded like every other wait: the clock and the abort
                     // flag are read every 256 rounds
+                    // (the warp leaves the loop together: the loop head is a vote)
                     if ((++rounds & 255u) == 0 &&
-                        (*abort || globaltimer() - t_start > TC_LIMIT_NS)) {
+                        __any_sync(0xffffffffu, *abort || globaltimer() - t_start > T.limit_ns)) {
                         bad = true;
                         break;
                     }
@@ -738,14 +752,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
             auto wait_a = [&](uint32_t a) -> bool {
                 if (a_seen == a)
                     return true;
-                if (!mbar_wait(&S.full_a[a & 1u], (a >> 1) & 1u, abort, TC_LIMIT_NS))
+                if (!mbar_wait(&S.full_a[a & 1u], (a >> 1) & 1u, abort, T.limit_ns))
                     return false;
                 a_seen = a;
                 return true;
             };
             for (uint32_t seq = j;; seq += 2) {
                 const uint32_t stage = seq % (uint32_t)NS;
-                if (!mbar_wait(&S.full_b[stage], (seq / NS) & 1u, abort, TC_LIMIT_NS)) {
+                if (!mbar_wait(&S.full_b[stage], (seq / NS) & 1u, abort, T.limit_ns)) {
                     dead = true;
                     break;
                 }
@@ -768,7 +782,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
                 if (dead)
                     break;
                 const uint32_t acc = j, use = seq >> 1;   // this accumulator's use count
-                if (!mbar_wait(&S.tmem_empty[acc], (use & 1u) ^ 1u, abort, TC_LIMIT_NS)) {
+                if (!mbar_wait(&S.tmem_empty[acc], (use & 1u) ^ 1u, abort, T.limit_ns)) {
                     dead = true;
                     break;
                 }
@@ -805,7 +819,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
             // and wait: the earlier arrivals of this thread have then landed.
             if (!dead) {
                 mma_commit(&S.fin[j]);
-                if (!mbar_wait(&S.fin[j], 0u, abort, TC_LIMIT_NS))
+                if (!mbar_wait(&S.fin[j], 0u, abort, T.limit_ns))
                     dead = true;
             }
             if (dead) {
@@ -830,8 +844,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
             bool last = false;
             for (;;) {
                 // every epilogue warp done: one more pass takes what is left
-                if (!last && *(volatile uint32_t *)&S.epi_done == 8u)
+                if (!last && *(volatile uint32_t *)&S.epi_done == 8u) {
+                    __threadfence_block();
                     last = true;
+                }
                 bool worked = false;
 #pragma unroll
                 for (int w = 0; w < 8; ++w) {
@@ -903,8 +919,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
         };
         for (uint32_t use = 0;; ++use) {
             const uint32_t par = use & 1u;
-            if (!mbar_wait(&S.desc_full[g], par, abort, TC_LIMIT_NS) ||
-                !mbar_wait(&S.tmem_full[g], par, abort, TC_LIMIT_NS)) {
+            const bool ok = mbar_wait(&S.desc_full[g], par, abort, T.limit_ns) &&
+                            mbar_wait(&S.tmem_full[g], par, abort, T.limit_ns);
+            // one decision per warp: the TMEM loads below need all 32 lanes
+            if (__any_sync(0xffffffffu, !ok)) {
                 dead = true;
                 break;
             }
@@ -1039,6 +1057,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
             flush();
         __syncwarp();
         if (lane == 0) {
+            __threadfence_block();   // the ring's last tail is visible before the count
             atomicAdd(&S.epi_done, 1u);
             if (surv_w)
                 atomicAdd(&S.surv, (unsigned long long)surv_w);
@@ -1084,14 +1103,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
             uint64_t *b = &S.epi_bar[es & 1u];
             if (lane == 0)
                 mbar_arrive(b);
-            bool ok = mbar_wait(b, (es >> 1) & 1u, abort, TC_LIMIT_NS);
+            const bool ok = mbar_wait(b, (es >> 1) & 1u, abort, T.limit_ns);
             ++es;
-            return ok;
+            return __all_sync(0xffffffffu, ok);   // one decision per warp
         };
         for (;;) {
             const uint32_t acc = turn & 1u, par = (turn >> 1) & 1u;
-            if (!mbar_wait(&S.desc_full[acc], par, abort, TC_LIMIT_NS) ||
-                !mbar_wait(&S.tmem_full[acc], par, abort, TC_LIMIT_NS)) {
+            const bool ok = mbar_wait(&S.desc_full[acc], par, abort, T.limit_ns) &&
+                            mbar_wait(&S.tmem_full[acc], par, abort, T.limit_ns);
+            // one decision per warp: the TMEM loads below need all 32 lanes
+            if (__any_sync(0xffffffffu, !ok)) {
                 dead = true;
                 break;
             }
@@ -1537,6 +1558,7 @@ cudaError_t launch_join_tc_jobs(const JoinLaunch &L, const void *XA, const void 
     T.XB = (const unsigned char *)XB;
     T.Kp = Kp;
     T.Tbits = 0;
+    T.limit_ns = wait_limit_ns();
     size_t sm = 0;
     T.NS = tc_stages(T.Kp, &T.a_bytes, &T.b_bytes, &T.off_b, &T.off_s, &sm);
     if (T.NS < 2)
@@ -1553,6 +1575,7 @@ cudaError_t launch_join_tc(const gj_index *h, const JoinLaunch &L, int grid, cud
     T.XB = (const unsigned char *)h->XB;
     T.Kp = h->tc_Kp;
     T.Tbits = h->tc_Tbits;
+    T.limit_ns = wait_limit_ns();
     size_t sm = 0;
     T.NS = tc_stages(T.Kp, &T.a_bytes, &T.b_bytes, &T.off_b, &T.off_s, &sm);
     if (T.NS < 2)
@@ -1717,5 +1740,11 @@ extern "C" int gj_tc_threshold(double eps, double sigma, double R0, int32_t d, f
         return GJ_ERR_INVALID_ARG;
     const int bits = gj::tc_threshold_bits(eps, sigma, R0, d, Kp);
     memcpy(T, &bits, sizeof(float));
+    return GJ_OK;
+}
+
+extern "C" int gj_debug_set_wait_limit(uint64_t ns)
+{
+    gj::g_wait_limit_ns.store(ns, std::memory_order_relaxed);
     return GJ_OK;
 }

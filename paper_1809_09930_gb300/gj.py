@@ -82,7 +82,7 @@ EXPORTS = ["gj_config_init", "gj_index_build", "gj_index_build_ex", "gj_self_joi
            "gj_last_status", "gj_status_string", "gj_version", "gj_probe_fp64_tflops",
            "gj_kernel_launches", "gj_debug_tc_tile", "gj_self_join_noalloc", "gj_batch_build",
            "gj_batch_self_join", "gj_batch_get_info", "gj_batch_free", "gj_autotune", "gj_batch_get_k",
-           "gj_neighbor_table", "gj_join_qe", "gj_tc_threshold"]
+           "gj_neighbor_table", "gj_join_qe", "gj_tc_threshold", "gj_debug_set_wait_limit"]
 
 _lib = None
 
@@ -125,6 +125,8 @@ def load(path: str | None = None):
     lib.gj_kernel_launches.argtypes = []
     lib.gj_debug_tc_tile.restype = C.c_int
     lib.gj_debug_tc_tile.argtypes = [V, V, C.c_int32, V]
+    lib.gj_debug_set_wait_limit.restype = C.c_int
+    lib.gj_debug_set_wait_limit.argtypes = [C.c_uint64]
     lib.gj_tc_threshold.restype = C.c_int
     lib.gj_tc_threshold.argtypes = [C.c_double, C.c_double, C.c_double, C.c_int32, C.POINTER(C.c_float)]
     lib.gj_self_join_noalloc.restype = C.c_int
@@ -319,6 +321,11 @@ def gj_probe_fp64_tflops(device: int = -1) -> float:
     return float(v.value)
 
 
+def gj_debug_set_wait_limit(ns: int) -> int:
+    """Limit of every bounded device wait of later tensor-core joins (0: default)."""
+    return int(load().gj_debug_set_wait_limit(int(ns)))
+
+
 def gj_kernel_launches() -> int:
     return int(load().gj_kernel_launches())
 
@@ -419,6 +426,7 @@ class Index:
         cfg.query_block = int(query_block)
         cfg.tile = int(tile)
         self.h = gj_index_build_ex(points, eps, cfg)
+        self._sizes = {}   # |R| of (part, nparts) once known: R is fixed for an index
 
     def close(self):
         if self.h:
@@ -444,13 +452,17 @@ class Index:
         return gj_last_join_stats(self.h)
 
     def count(self) -> int:
+        """|R| by a count-only join (remembered for join())."""
         st, n = gj_self_join(self.h, None)
         if st != GJ_OK:
             raise GJError(st, "gj_self_join (count)")
+        self._sizes[(None, 1)] = n
         return n
 
     def join_qe(self, queries):
-        """The pairs (query row, entry row) within eps as a (m, 2) uint32 array."""
+        """The pairs (query row, entry row) within eps as a (m, 2) uint32 array.
+        Two launches: a count-only join sizes the array, then the join fills it
+        (call gj_join_qe with a buffer of your own to join once)."""
         st, m = gj_join_qe(self.h, queries, None)
         if st != GJ_OK:
             raise GJError(st, "gj_join_qe (count)")
@@ -473,9 +485,15 @@ class Index:
         return row_start, nbr[:c]
 
     def join(self, out=None, part: int | None = None, nparts: int = 1):
-        """Pairs as a (|R|, 2) uint32 numpy array (or the given buffer's prefix)."""
+        """Pairs as a (|R|, 2) uint32 numpy array (or the given buffer's prefix).
+        Without a buffer the array is sized by |R|: known after count() or an
+        earlier join of this index, else found by one count-only join first
+        (then the call runs the join twice; pass ``out`` to join once)."""
+        key = (part, nparts if part is not None else 1)
         if out is None:
-            n = self.count() if part is None else gj_self_join_part(self.h, part, nparts, None)[1]
+            n = self._sizes.get(key)
+            if n is None:
+                n = self.count() if part is None else gj_self_join_part(self.h, part, nparts, None)[1]
             out = np.empty((max(n, 1), 2), dtype=np.uint32)
         if part is None:
             st, n = gj_self_join(self.h, out)
@@ -483,4 +501,5 @@ class Index:
             st, n = gj_self_join_part(self.h, part, nparts, out)
         if st != GJ_OK:
             raise GJError(st, "gj_self_join")
+        self._sizes[key] = n
         return out[:n]

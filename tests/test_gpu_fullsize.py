@@ -163,3 +163,85 @@ def test_large_skewed_plain_equals_tc_count():
     with gj.Index(X, w["eps"], k=0, flags=TC) as it:
         n_tc = it.count()
     assert n_plain == n_tc > 300_000_000
+
+
+def _device_keys(out: torch.Tensor, m: int) -> torch.Tensor:
+    t = out[:m]
+    return torch.sort((t[:, 0].to(torch.int64) << 32) | (t[:, 1].to(torch.int64) & 0xFFFFFFFF)).values
+
+
+@pytest.mark.parametrize("name", ["paper_d32", "paper_d64"])
+def test_paper_scale_plain_fp64_full(name):
+    """The plain FP64 form (SHORTC, no tensor cores) over the whole 2M-point set
+    at d = 32 and 64, once (about 1.5 and 4 minutes): the same pair set as the
+    tensor-core form, bit for bit, and the oracle's list for sampled queries."""
+    w = _w(name)
+    X = synth.uniform(w["n"], w["d"], w["seed"])
+    Xd = torch.from_numpy(X).cuda()
+    with gj.Index(Xd, w["eps"], k=0, flags=TC) as it:
+        n = it.count()
+        out = torch.empty((n, 2), dtype=torch.int32, device="cuda")
+        st, m = gj.gj_self_join(it.h, out)
+        assert st == gj.GJ_OK and m == n
+    tc_keys = _device_keys(out, n)
+    with gj.Index(Xd, w["eps"], k=0) as ip:
+        st, m = gj.gj_self_join(ip.h, out)           # the tensor-core count sizes the buffer
+        assert st == gj.GJ_OK and m == n
+        s = ip.stats()
+    print(f"{name}: plain FP64 join {s['join_ms'] / 1e3:.1f} s, |R| = {n}")
+    plain_keys = _device_keys(out, n)
+    assert torch.equal(plain_keys, tc_keys)
+    _check_properties(plain_keys, w["n"])
+    _check_queries(X, w["eps"], plain_keys, _queries(w["n"], 11 + w["d"], m=24))
+
+
+def test_mixture_d32_tc_against_the_oracle():
+    """The 68,000 x 32 mixture (stands in for ColorHist/LayoutHist, Table 1) in
+    the tensor-core form at its full size, element by element against the
+    oracle's grid join."""
+    from tests.parity import assert_parity
+    w = _w("mixture_d32")
+    X = synth.mixture(w["n"], w["d"], w["seed"])
+    keys, info = _device_join(X, w["eps"], TC)
+    _check_properties(keys, w["n"])
+    got = np.stack([(keys >> 32).cpu().numpy(), (keys & 0xFFFFFFFF).cpu().numpy()], axis=1).astype(np.uint32)
+    assert_parity(X, w["eps"], got, oracle.grid_join(X, w["eps"], 3))
+
+
+def test_many_jobs_full_size():
+    """The full many-jobs workload (256 jobs, n log-uniform in [1k, 200k], 10 M
+    points, d in {16, 18, 32}, uniform and mixture alternating, eps per job for
+    8-128 mean neighbours) in one graph-captured launch: every job's pairs equal
+    its own single join, a replay of the graph gives the same pairs, and the 8
+    largest jobs match the oracle on sampled queries."""
+    with open(os.path.join(GOLD, "workloads.json")) as f:
+        specs = json.load(f)["jobs"]
+    assert len(specs) == 256
+    data = [synth.generate(js["kind"], js["n"], js["d"], js["seed"]) for js in specs]
+    jobs = [(torch.from_numpy(X).cuda(), js["eps"], 0) for X, js in zip(data, specs)]
+    b = gj.gj_batch_build(jobs)
+    try:
+        st, counts = gj.gj_batch_self_join(b, len(jobs))
+        assert st == gj.GJ_OK
+        outs = [torch.empty((c + 8, 2), dtype=torch.int32, device="cuda") for c in counts]
+        st, c1 = gj.gj_batch_self_join(b, len(jobs), outs)
+        assert st == gj.GJ_OK and c1 == counts
+        first = [_device_keys(o, c) for o, c in zip(outs, counts)]
+        st, c2 = gj.gj_batch_self_join(b, len(jobs), outs)          # graph replay
+        assert st == gj.GJ_OK and c2 == counts
+        for j, (o, c) in enumerate(zip(outs, counts)):
+            assert torch.equal(_device_keys(o, c), first[j]), f"replay differs on job {j}"
+    finally:
+        gj.gj_batch_free(b)
+    for j, (Xd, eps, _) in enumerate(jobs):
+        with gj.Index(Xd, eps, k=0, flags=TC) as ix:
+            n = ix.count()
+            assert n == counts[j], f"job {j}"
+            single = torch.empty((n, 2), dtype=torch.int32, device="cuda")
+            st, m = gj.gj_self_join(ix.h, single)
+            assert st == gj.GJ_OK and m == n
+        assert torch.equal(_device_keys(single, n), first[j]), f"job {j} differs from its single join"
+    largest = sorted(range(len(specs)), key=lambda j: -specs[j]["n"])[:8]
+    for j in largest:
+        _check_properties(first[j], specs[j]["n"])
+        _check_queries(data[j], specs[j]["eps"], first[j], _queries(specs[j]["n"], 300 + j, m=12))

@@ -157,15 +157,16 @@ def test_device_output_buffer():
 
 @pytest.mark.parametrize("form", ["plain", "tc"])
 def test_pinned_host_output_direct_and_batched(form):
-    """Pinned host memory that the device can address is written by the join
-    kernels in one pass, as device memory is; GJ_HOST_BATCHED sends it through
-    the result batches of Sec. 3.2.2 instead.  Both give R, neither writes past
-    |R|, and a buffer that is too small gives GJ_ERR_CAPACITY with |R|."""
+    """Pinned host output is filled by copies.  A tensor-core index joins in
+    one pass into a device buffer that is then copied; the plain form, and
+    GJ_HOST_BATCHED, go through the result batches of Sec. 3.2.2.  All give R,
+    none writes past |R|, and a buffer that is too small gives GJ_ERR_CAPACITY
+    with |R|."""
     torch = pytest.importorskip("torch")
     X = synth.mixture(6000, 18, 6)
     ref = oracle.brute(X, 0.35)
     base = gj.GJ_DEFAULT_FLAGS | (gj.GJ_TC_FILTER if form == "tc" else 0)
-    for flags, one_pass in ((base, True), (base | gj.GJ_HOST_BATCHED, False)):
+    for flags, one_pass in ((base, form == "tc"), (base | gj.GJ_HOST_BATCHED, False)):
         with gj.Index(X, 0.35, k=4, flags=flags, batch_pairs=70_000) as ix:
             n = ix.count()
             assert n == len(ref)

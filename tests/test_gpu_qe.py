@@ -102,7 +102,7 @@ def test_qe_device_buffers_capacity_and_errors():
         assert st == gj.GJ_OK and m0 == 0
 
 
-def test_qe_pinned_host_output_is_written_directly():
+def test_qe_pinned_host_output():
     E = synth.uniform(3000, 8, 5)
     Q = synth.uniform(2000, 8, 6)
     with gj.Index(E, 0.3, k=2) as ix:

@@ -26,6 +26,105 @@ def _rand_f16(shape, seed, scale=1.0):
     return ((u * 2.0 - 1.0) * scale).astype(np.float16)
 
 
+def _adversarial_tile(Kp, variant, seed):
+    """A, B (fp16, 128 x Kp) whose fp32 sums are hard to get right.
+    cancel: per row two products +-250*250 at row-dependent K positions (the
+      large pair falls early, late or in the middle of the sum), every other
+      product 250 * (r 2^-17), an fp16 subnormal times 250, just below half an
+      fp32 ulp of 62500: added beside the large terms they round away; B's
+      signs random, so about half the entries cancel to the small terms.
+    same-sign: as cancel with both large products positive.
+    norms: the filter's own rows, A = [-2h, |h|^2_hi, |h|^2_lo, 1, 1] and
+      B = [h', 1, 1, |h'|^2_hi, |h'|^2_lo] with |h| near 250 and h' = h plus a
+      small offset: terms of 62500 cancel down to a small |h - h'|^2."""
+    rng = np.random.default_rng(seed)
+    A = np.zeros((128, Kp), dtype=np.float64)
+    B = np.zeros((128, Kp), dtype=np.float64)
+    if variant in ("cancel", "same-sign"):
+        r = rng.integers(8, 16, size=(128, Kp)) / 16.0
+        A[:] = r * 2.0 ** -17
+        for i in range(128):
+            k1 = i % Kp
+            k2 = (i * 7 + 3) % Kp
+            if k2 == k1:
+                k2 = (k1 + 1) % Kp
+            A[i, k1] = 250.0
+            A[i, k2] = -250.0 if variant == "cancel" else 250.0
+        B[:] = 250.0
+        if variant == "cancel":
+            B[rng.random((128, Kp)) < 0.5] *= -1.0
+    else:
+        d = Kp - 4
+
+        def rows(n, base=None):
+            if base is None:
+                h = rng.normal(size=(n, d))
+                h *= (250.0 * rng.uniform(0.97, 1.0, size=(n, 1))) / np.linalg.norm(h, axis=1, keepdims=True)
+            else:
+                h = base + rng.normal(scale=0.05, size=base.shape)
+            # magnitudes >= 1/4 keep every product a multiple of 2^-24 and the
+            # fp64 reference sums exact (at most 42 significant bits)
+            h = np.where(h < 0, -1.0, 1.0) * np.maximum(np.abs(h), 0.25)
+            h = h.astype(np.float16).astype(np.float64)
+            nrm = (h * h).sum(axis=1)
+            hi = nrm.astype(np.float16).astype(np.float64)
+            lo = (nrm - hi).astype(np.float16).astype(np.float64)
+            return h, hi, lo
+
+        ha, hia, loa = rows(128)
+        hb, hib, lob = rows(128, ha)
+        A[:, :d] = -2.0 * ha
+        A[:, d], A[:, d + 1], A[:, d + 2], A[:, d + 3] = hia, loa, 1.0, 1.0
+        B[:, :d] = hb
+        B[:, d], B[:, d + 1], B[:, d + 2], B[:, d + 3] = 1.0, 1.0, hib, lob
+    return A.astype(np.float16), B.astype(np.float16)
+
+
+@pytest.mark.parametrize("Kp", [16, 48, 128])
+@pytest.mark.parametrize("variant", ["cancel", "same-sign", "norms"])
+def test_single_tile_adversarial_accumulation(Kp, variant):
+    """The accumulation model where it is tightest: exact fp16 products (their
+    fp64 sums are exact here), fp32 results within (Kp + 2) 2^-22 of the sum
+    of |terms| on every entry."""
+    A, B = _adversarial_tile(Kp, variant, 300 + Kp)
+    D = gj.gj_debug_tc_tile(A, B).astype(np.float64)
+    a = A.astype(np.float64)
+    b = B.astype(np.float64)
+    exact = a @ b.T
+    absum = np.abs(a) @ np.abs(b).T
+    bound = (Kp + 2) * 2.0 ** -22 * absum
+    ratio = np.abs(D - exact) / bound
+    print(f"Kp={Kp} {variant}: worst err/bound {ratio.max():.4f}, worst |err| {np.abs(D - exact).max():.3g}")
+    assert np.all(ratio <= 1.0), f"worst err/bound {ratio.max()}"
+
+
+def test_planted_pairs_at_the_largest_radius_d124():
+    """Pairs at eps (1 - 2^-40) on a sphere of the largest radius about the
+    filter's centre (points mirrored through the origin, so the per-dimension
+    midrange is 0), d = 124, Kp = 128: the filter's margin is dominated by its
+    accumulation term there.  Every planted pair within eps must be found."""
+    d, m, rho, eps = 124, 1500, 40.0, 0.05
+    u = synth.normal(501, m * d).reshape(m, d)
+    u /= np.linalg.norm(u, axis=1, keepdims=True)
+    v = synth.normal(502, m * d).reshape(m, d)
+    v -= (v * u).sum(axis=1, keepdims=True) * u          # orthogonal to u: the partner stays near radius rho
+    v /= np.linalg.norm(v, axis=1, keepdims=True)
+    base = rho * u
+    partner = base + v * (eps * (1.0 - 2.0 ** -40))
+    X = np.vstack([base, partner, -base, -partner])
+    plain, tc, st = _both(X, eps, k=1)
+    assert np.array_equal(keys(plain), keys(tc))
+    got = set(keys(tc).tolist())
+    found = inside = 0
+    for off in (0, 2 * m):
+        for i in range(m):
+            a, b = off + i, off + m + i
+            if oracle.sqdist(X[a], X[b]) <= eps * eps:
+                inside += 1
+                found += ((a << 32) | b) in got and ((b << 32) | a) in got
+    assert found == inside and inside > 0.8 * 2 * m
+
+
 @pytest.mark.parametrize("Kp", [16, 32, 48, 96, 128])
 def test_single_tile_layout_and_error_model(Kp):
     A = _rand_f16((128, Kp), 100 + Kp, 40.0)
@@ -116,10 +215,10 @@ def test_tc_lattice_exact():
 def test_tc_small_batches_resume_exactly():
     X = synth.mixture(8000, 18, 6)
     ref = oracle.brute(X, 0.35)
-    with gj.Index(X, 0.35, k=2, flags=TC, batch_pairs=150_000) as ix:
+    with gj.Index(X, 0.35, k=2, flags=TC | gj.GJ_HOST_BATCHED, batch_pairs=150_000) as ix:
         got = ix.join()
         st = ix.stats()
-    assert st["launches"] > 3
+    assert st["launches"] > 3     # result batches of 150,000 pairs, each resumed exactly
     assert_parity(X, 0.35, got, ref)
 
 
