@@ -481,12 +481,16 @@ def bench_qe(args):
     from paper_1809_09930_gb300 import gj
     with open(WORKLOADS) as f:
         w = json.load(f)["paper_d16"]
-    steps = args.steps if args.steps is not None else 3
+    # (the tensor-core join takes ~40 ms: more steps give the clock sampler a
+    # second of load)
+    steps = args.steps if args.steps is not None else (30 if args.form == "tc" else 3)
     stream = torch.cuda.current_stream()
     E = torch.from_numpy(synth.uniform(args.n, 16, w["seed"])).cuda()
     Qh = synth.uniform(args.nq, 16, w["seed"] + 7919)
     Q = torch.from_numpy(Qh).cuda()
-    ix = gj.Index(E, w["eps"], k=0, stream=stream.cuda_stream)
+    tc = args.form == "tc"
+    flags = gj.GJ_DEFAULT_FLAGS | (gj.GJ_TC_FILTER if tc else 0)
+    ix = gj.Index(E, w["eps"], k=0, flags=flags, stream=stream.cuda_stream)
     st, m = gj.gj_join_qe(ix.h, Q, None)
     out = torch.empty((m + 16, 2), dtype=torch.int32, device="cuda")
     for _ in range(args.warmup):
@@ -498,7 +502,7 @@ def bench_qe(args):
     l0 = gj.gj_kernel_launches()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
-    join_ms, dims, cand = 0.0, 0, 0
+    join_ms, dims, cand, surv = 0.0, 0, 0, 0
     for _ in range(steps):
         st, m2 = gj.gj_join_qe(ix.h, Q, out)
         if st != gj.GJ_OK or m2 != m:
@@ -507,6 +511,7 @@ def bench_qe(args):
         join_ms += s["join_ms"]
         dims += s["dims"]
         cand += s["candidates"]
+        surv += s["tc_survivors"]
     ev1.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
@@ -520,8 +525,23 @@ def bench_qe(args):
         gj.gj_join_qe(ix.h, hq, hout)
     e2e_s = time.perf_counter() - t0
     ix.close()
-    achieved = 3.0 * dims / (join_ms * 1e-3) / 1e12
-    peak = 0.75 * fp64
+    if tc:
+        # contraction work: 2*d FLOPs per query x entry candidate pair
+        with open(PEAKS) as f:
+            pk = json.load(f)
+        peak = pk.get("bf16_tflops_sustained") or pk.get("bf16_tflops")
+        achieved = 2.0 * 16 * cand / (join_ms * 1e-3) / 1e12
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "k_join_tc (asymmetric)",
+                "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (fp16 runs at the bf16 rate)",
+                "join_ms_per_step": join_ms / steps, "survivors_per_step": surv / steps}
+    else:
+        achieved = 3.0 * dims / (join_ms * 1e-3) / 1e12
+        peak = 0.75 * fp64
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "k_join_plain (asymmetric)",
+                "peak_source": "FP64 FMA probe measured in this run x 3/4 (DADD+DFMA mix)",
+                "join_ms_per_step": join_ms / steps}
     cb = None
     if not args.no_baseline:
         import oracle
@@ -535,13 +555,11 @@ def bench_qe(args):
         "metric": "distance evals/s (similarity join Q join_eps E, exact pair set)",
         "value": cand / (ms * 1e-3), "unit": "distance evals/s", "n_gpus": 1, "steps": steps,
         "warmup": args.warmup, "ms_per_step": ms / steps, "higher_is_better": True, "scaling": "strong",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": "f16xf16->f32 filter + f64 recheck" if tc else "f64", "data": "synthetic",
         "config": {"workload": f"Q join_eps E: {args.nq} uniform queries x {args.n} uniform entries, d=16, "
-                               f"eps {w['eps']}", "pairs": m,
+                               f"eps {w['eps']}", "form": args.form, "pairs": m,
                    "step": "gj_join_qe (query side build + one join launch) into a device buffer"},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                     "traffic": None, "kernel": "k_join_plain (asymmetric)",
-                     "peak_source": "FP64 FMA probe measured in this run x 3/4 (DADD+DFMA mix)"},
+        "roofline": roof,
         "cpu_baseline": cb,
         "e2e": {"value": cand / e2e_s, "unit": "distance evals/s", "h2d_bytes_per_step": int(Qh.nbytes),
                 "d2h_bytes_per_step": 8 * m},

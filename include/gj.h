@@ -227,7 +227,14 @@ int gj_self_join_part(gj_index *h, int32_t part, int32_t nparts, gj_pair *pairs_
  * E's grid (its REORDER permutation, cell width and origin), sorted by cell
  * and by E's SORTIDU dimension; each query cell searches all adjacent
  * non-empty entry cells; distances are the FP64 SHORTC sums of the self-join.
- *   h          an index over E (any flags; the join uses the plain FP64 form)
+ * The join runs in the index's form: the plain FP64 kernel, or, for an index
+ * built with GJ_TC_FILTER, the tensor-core filter and its FP64 recheck (the
+ * same pair set).  The tensor-core form packs the queries as fp16 A rows under
+ * the entries' centre, with one power-of-two scale for both sets: queries
+ * farther from that centre than every entry give a smaller scale, for which
+ * the entries are re-packed for the call (more device memory, a looser
+ * filter, the same result).
+ *   h          an index over E (any flags)
  *   queries    row-major nq x d FP64 (d = E's), host or device memory (of
  *              any device); copied, the caller keeps ownership
  *   pairs_out  host memory or device memory of the handle's device for cap

@@ -196,8 +196,17 @@ int tc_prepare(gj_index *h, const double *stats_host, const int *perm, cudaStrea
 cudaError_t launch_join_tc(const gj_index *h, const JoinLaunch &L, int grid, cudaStream_t s, bool direct);
 size_t tc_staging_pairs_per_cta();
 int tc_threshold_bits(double eps, double sigma, double R0, int d, int Kp);
+// XA or XB may be null (only the other operand is written)
 cudaError_t tc_pack_into(const double *X, int64_t n, int64_t npad, int d, int Kp, double sigma, const double *centre,
                          int64_t row_off, void *XA, void *XB, cudaStream_t s);
+// largest distance of n points (structure-of-arrays, row stride npad) from
+// centre, widened by 1 + 2^-30; synchronous
+cudaError_t tc_radius(const double *X, int64_t n, int64_t npad, int d, const double *centre, double *R0,
+                      cudaStream_t s);
+double tc_sigma_for(double R0);
+// direct form over explicit operands (L.ix.asym: Q join_eps E)
+cudaError_t launch_join_tc_ops(const JoinLaunch &L, const void *XA, const void *XB, int Kp, int Tbits, int grid,
+                               cudaStream_t s);
 // job_cycles (nullable): per-job SM cycles between the epilogue's item ends,
 // summed over CTAs (the autotuner's per-job timing)
 cudaError_t launch_join_tc_jobs(const JoinLaunch &L, const void *XA, const void *XB, int Kp, const TcJob *jobs,

@@ -7,12 +7,15 @@
 // permutation, cell widths and origin, sorted by cell and by the SORTIDU
 // dimension, gathered into the structure-of-arrays layout), every query cell
 // gets the list of all adjacent non-empty entry cells (no symmetry to exploit),
-// and the plain FP64 SHORTC kernel runs in its asymmetric mode: queries from
-// the query array, candidates from the entries, one orientation (q, e) per
-// pair.  One launch writes the pairs straight into the caller's buffer when
-// the device can address it (device memory, pinned host memory), else into a
-// device buffer of cap pairs that is then copied to the host, with warp-aggregated
-// atomics and counts every pair, so a result larger than cap is reported with
+// and a join kernel runs in its asymmetric mode: queries from the query array,
+// candidates from the entries, one orientation (q, e) per pair.  The kernel is
+// the index's own form: the plain FP64 SHORTC kernel, or for an index built
+// with GJ_TC_FILTER the tensor-core filter with its FP64 recheck (query A rows
+// and entry B rows packed under one centre and one scale that covers both
+// sets, so the filter's margin holds for every query-entry pair).  One launch
+// writes the pairs straight into the caller's device buffer, or into a device
+// buffer of cap pairs that is then copied to the host, with warp-aggregated
+// atomics, and counts every pair, so a result larger than cap is reported with
 // its size.
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -59,16 +62,25 @@ extern "C" int gj_join_qe(gj_index *h, const double *queries, int64_t nq, gj_pai
         return GJ_ERR_INVALID_ARG;   // another device's memory
     cudaStream_t s = h->stream;
     const int d = h->info.d;
+    const bool tc = h->tc_ready;
     // query blocks small enough that every CTA of the persistent grid gets
     // about eight (few queries against many entries would otherwise leave
     // most of the grid idle behind a few long blocks); blocks of at most 64
-    // also shrink the kernel's query tile, which may fit more CTAs per SM
-    int per_sm = plain_ctas_per_sm(d, h->plain_ct, QB);
-    if (per_sm < 1)
-        return GJ_ERR_UNSUPPORTED;
-    const int qb = (int)std::max<int64_t>(32, std::min<int64_t>(QB_PLAIN, (nq / (8 * (int64_t)h->sms * per_sm)) & ~7));
-    per_sm = plain_ctas_per_sm(d, h->plain_ct, qb);
-    const int grid = h->sms * per_sm;
+    // also shrink the plain kernel's query tile, which may fit more CTAs per
+    // SM.  Tensor-core blocks hold at most 120 queries, so the 128-row A tile
+    // from the block's first row rounded down to 8 covers the block.
+    int qb = 0, grid = 0;
+    if (tc) {
+        qb = (int)std::max<int64_t>(32, std::min<int64_t>(120, (nq / (8 * (int64_t)h->sms)) & ~7));
+        grid = h->sms;
+    } else {
+        int per_sm = plain_ctas_per_sm(d, h->plain_ct, QB);
+        if (per_sm < 1)
+            return GJ_ERR_UNSUPPORTED;
+        qb = (int)std::max<int64_t>(32, std::min<int64_t>(QB_PLAIN, (nq / (8 * (int64_t)h->sms * per_sm)) & ~7));
+        per_sm = plain_ctas_per_sm(d, h->plain_ct, qb);
+        grid = h->sms * per_sm;
+    }
 
     // queries on the device, finite
     double *Qd = nullptr;
@@ -109,7 +121,41 @@ extern "C" int gj_join_qe(gj_index *h, const double *queries, int64_t nq, gj_pai
         return GJ_OK;
     }
 
-    // the asymmetric plain kernel
+    // tensor-core operands: the scale must keep every |h| of both sets at
+    // most 250, so it comes from the larger radius about the entries' centre;
+    // the entries' B rows are reused when that scale is theirs
+    void *XAq = nullptr, *XBt = nullptr;
+    const void *XBop = nullptr;
+    int Tbits = 0;
+    if (tc) {
+        double R0q = 0.0;
+        const int Kp = h->tc_Kp;
+        e = tc_radius(qs.XQ, nq, qs.qnpad, d, h->tc_centre, &R0q, s);
+        const double R0 = std::max(h->tc_R0, R0q);
+        const double sigma = tc_sigma_for(R0);
+        const size_t abytes = (size_t)(qs.qnpad + 512) * Kp * 2;
+        if (e == cudaSuccess) e = dev_alloc(&XAq, abytes, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(XAq, 0, abytes, s);
+        if (e == cudaSuccess) e = tc_pack_into(qs.XQ, nq, qs.qnpad, d, Kp, sigma, h->tc_centre, 0, XAq, nullptr, s);
+        XBop = h->XB;
+        if (e == cudaSuccess && sigma != h->tc_sigma) {
+            const size_t bbytes = (size_t)(h->npad + 512) * Kp * 2;
+            e = dev_alloc(&XBt, bbytes, s);
+            if (e == cudaSuccess) e = cudaMemsetAsync(XBt, 0, bbytes, s);
+            if (e == cudaSuccess)
+                e = tc_pack_into(h->X, h->info.n, h->npad, d, Kp, sigma, h->tc_centre, 0, nullptr, XBt, s);
+            XBop = XBt;
+        }
+        Tbits = tc_threshold_bits(h->info.eps, sigma, R0, d, Kp);
+        if (e != cudaSuccess) {
+            dev_free(XAq, s);
+            dev_free(XBt, s);
+            free_query_side(&qs, s);
+            return status_of(e);
+        }
+    }
+
+    // the asymmetric join kernel
     JoinCtl *ctl = nullptr;
     uint32_t *queue = nullptr;
     gj_pair *dbuf = nullptr;
@@ -166,7 +212,8 @@ extern "C" int gj_join_qe(gj_index *h, const double *queries, int64_t nq, gj_pai
     L.cap = out ? cap : 0;
     if (e == cudaSuccess) e = cudaMemsetAsync(ctl, 0, sizeof(JoinCtl), s);
     if (e == cudaSuccess) e = cudaEventRecord(ev0, s);
-    if (e == cudaSuccess) e = launch_join_plain_direct(L, grid, s);
+    if (e == cudaSuccess)
+        e = tc ? launch_join_tc_ops(L, XAq, XBop, h->tc_Kp, Tbits, grid, s) : launch_join_plain_direct(L, grid, s);
     if (e == cudaSuccess) e = cudaEventRecord(ev1, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&hctl, ctl, sizeof(JoinCtl), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -176,11 +223,14 @@ extern "C" int gj_join_qe(gj_index *h, const double *queries, int64_t nq, gj_pai
         kms = ms;
         if (hctl.err & kErrTimeout)
             st = GJ_ERR_TIMEOUT;
+        else if (hctl.err)
+            st = GJ_ERR_CUDA;
         total = out ? hctl.pos : hctl.counted;
         h->last = gj_join_stats{};
         h->last.pairs = total;
         h->last.evaluated = hctl.evaluated;
         h->last.dims = hctl.dims;
+        h->last.tc_survivors = hctl.survivors;
         h->last.candidates = qs.candidates;
     }
     h->last.join_ms = kms;
@@ -192,6 +242,8 @@ extern "C" int gj_join_qe(gj_index *h, const double *queries, int64_t nq, gj_pai
     cudaFree(ctl);
     cudaFree(queue);
     cudaFree(dbuf);
+    dev_free(XAq, s);
+    dev_free(XBt, s);
     free_query_side(&qs, s);
     if (e != cudaSuccess)
         return status_of(e);

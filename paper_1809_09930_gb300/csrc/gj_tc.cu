@@ -168,8 +168,11 @@ __device__ __forceinline__ int64_t tc_upper_u(const double *__restrict__ U, int6
 // Exact test of one surviving candidate: the plain path's FP64 SHORTC sum in
 // REORDER order (same operations in the same order, so the same decision).
 // Coordinates are fetched 16 dimensions at a time with independent loads, so
-// a recheck costs about d/16 memory round trips instead of d.
-__device__ __forceinline__ bool tc_exact(const double *__restrict__ X, int64_t npad, int d, long long e2bits,
+// a recheck costs about d/16 memory round trips instead of d.  The query
+// comes from Xq (the entries themselves in a self-join, the query array in
+// Q join_eps E), the candidate from the entries X.
+__device__ __forceinline__ bool tc_exact(const double *__restrict__ Xq, int64_t qnpad,
+                                         const double *__restrict__ X, int64_t npad, int d, long long e2bits,
                                          uint32_t qpos, uint32_t cpos)
 {
     double s = 0.0;
@@ -178,7 +181,7 @@ __device__ __forceinline__ bool tc_exact(const double *__restrict__ X, int64_t n
 #pragma unroll
         for (int t = 0; t < 16; ++t) {
             if (j0 + t < d) {
-                a[t] = X[(int64_t)(j0 + t) * npad + qpos];
+                a[t] = Xq[(int64_t)(j0 + t) * qnpad + qpos];
                 b[t] = X[(int64_t)(j0 + t) * npad + cpos];
             }
         }
@@ -197,6 +200,9 @@ __device__ __forceinline__ bool tc_exact(const double *__restrict__ X, int64_t n
 
 // Recheck the warp's queued survivors (one per lane per round) and emit the
 // exact pairs into the staging half (or count them).  Called by all 32 lanes.
+// A self-join emits both orientations of a pair (one for i = j); Q join_eps E
+// (asym) emits (query, entry) once.
+template <bool ASYM>
 __device__ __noinline__ void tc_flush_survivors(const TcLaunch *__restrict__ T, const uint32_t *sq,
                                                 const uint32_t *sc, uint32_t n, gj_pair *stg, uint32_t *cnt,
                                                 uint32_t *flush_req, unsigned long long *counted, uint32_t job,
@@ -205,6 +211,9 @@ __device__ __noinline__ void tc_flush_survivors(const TcLaunch *__restrict__ T, 
     const int lane = threadIdx.x & 31;
     const double *__restrict__ X = T->J.ix.X;
     const int64_t npad = T->J.ix.npad;
+    const double *__restrict__ Xq = ASYM ? T->J.ix.XQ : X;
+    const int64_t qnpad = ASYM ? T->J.ix.qnpad : npad;
+    const uint32_t *__restrict__ qorig = ASYM ? T->J.ix.qorig : T->J.ix.orig;
     const TcJob *jp = T->jobs ? &T->jobs[job] : nullptr;
     const long long e2bits = __double_as_longlong(jp ? jp->e2 : T->J.ix.e2);
     // a job's dimensions past its own d are zero in the combined layout and
@@ -217,9 +226,9 @@ __device__ __noinline__ void tc_flush_survivors(const TcLaunch *__restrict__ T, 
         if (i < n) {
             qpos = sq[i];
             cpos = sc[i];
-            keep = tc_exact(X, npad, d, e2bits, qpos, cpos);
+            keep = tc_exact(Xq, qnpad, X, npad, d, e2bits, qpos, cpos);
         }
-        const uint32_t np = keep ? ((qpos != cpos) ? 2u : 1u) : 0u;
+        const uint32_t np = keep ? ((!ASYM && qpos != cpos) ? 2u : 1u) : 0u;
         if (stg == nullptr && jp == nullptr && dpos == nullptr) {
             *counted += np;
             continue;
@@ -255,7 +264,7 @@ __device__ __noinline__ void tc_flush_survivors(const TcLaunch *__restrict__ T, 
                 o64 = atomicAdd(dpos, (unsigned long long)tot);
             o64 = __shfl_sync(0xffffffffu, o64, 0) + incl - np;
             if (np) {
-                const uint32_t a = T->J.ix.orig[qpos], b = T->J.ix.orig[cpos];
+                const uint32_t a = qorig[qpos], b = T->J.ix.orig[cpos];
                 if (o64 < T->J.cap)
                     T->J.out[o64] = gj_pair{a, b};
                 if (np == 2 && o64 + 1 < T->J.cap)
@@ -299,6 +308,7 @@ __device__ __forceinline__ uint32_t hit_mask32(const uint32_t (&v)[32], float Tf
 // valid survivors marked in each lane's hit mask (warp-aggregated), flushing
 // the queue through the FP64 recheck when it would overflow.  Returns the new
 // queue length.
+template <bool ASYM>
 __device__ __forceinline__ uint32_t tc_queue_bits(const TcLaunch *__restrict__ T, uint32_t mask, uint32_t col0,
                                                uint32_t qpos, uint32_t r0,
                                                uint32_t *sq, uint32_t *sc, uint32_t nq, gj_pair *stg, uint32_t *cnt,
@@ -315,9 +325,10 @@ __device__ __forceinline__ uint32_t tc_queue_bits(const TcLaunch *__restrict__ T
             break;
         const uint32_t cpos = r0 + col0 + (have ? (uint32_t)(__ffs(mask) - 1) : 0u);
         mask &= mask - 1u;
-        // the mask holds valid rows only; j >= i keeps one orientation (rows of
-        // the other searched cells all lie after the query cell)
-        const bool h = have && cpos >= qpos;
+        // the mask holds valid rows only; in a self-join j >= i keeps one
+        // orientation (rows of the other searched cells all lie after the
+        // query cell); Q join_eps E keeps every marked candidate
+        const bool h = have && (ASYM || cpos >= qpos);
         const unsigned bal = __ballot_sync(0xffffffffu, h);
         if (!bal)
             continue;
@@ -325,7 +336,7 @@ __device__ __forceinline__ uint32_t tc_queue_bits(const TcLaunch *__restrict__ T
         if (nq + k > (uint32_t)TC_SQ) {
             unsigned long long c = 0;
             __syncwarp();
-            tc_flush_survivors(T, sq, sc, nq, stg, cnt, flush_req, &c, job, dpos);
+            tc_flush_survivors<ASYM>(T, sq, sc, nq, stg, cnt, flush_req, &c, job, dpos);
             __syncwarp();
             if (c)
                 atomicAdd(counted_sh, c);   // each lane counted its own pairs
@@ -350,9 +361,10 @@ __device__ __forceinline__ uint32_t tc_queue_bits(const TcLaunch *__restrict__ T
 // reservation per warp, so the epilogue needs no agreement between warps and
 // runs as two groups of four warps, one per accumulator, that work on
 // alternate tiles.
-template <bool DIRECT>
+template <bool DIRECT, bool ASYM>
 __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
 {
+    static_assert(DIRECT || !ASYM, "Q join_eps E runs in the direct form");
     extern __shared__ __align__(1024) unsigned char smem[];
     TcShared &S = *reinterpret_cast<TcShared *>(smem + T.off_s);
     unsigned char *Abuf = smem;
@@ -454,7 +466,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
             if (dead)
                 break;
             ++nitem;
-            const int64_t cell_end = L.ix.cell_start[it.cell + 1];
+            // Q join_eps E: the item's cell is a query cell (its adjacency lists
+            // every adjacent entry cell; no own-cell window)
+            const bool asym = ASYM;
+            const int64_t cell_end = asym ? 0 : L.ix.cell_start[it.cell + 1];
             const int64_t nb_begin = L.ix.adj_start[it.cell], nb_end = L.ix.adj_start[it.cell + 1];
             const uint32_t job = T.jobs ? it.pad : 0u;
             const int u = T.jobs ? T.jobs[job].u : L.ix.u;
@@ -462,8 +477,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
             const uint32_t jtb = T.jobs ? (uint32_t)T.jobs[job].Tbits : (uint32_t)T.Tbits;
             double ulo = 0.0, uhi = 0.0;
             if (u >= 0) {
-                ulo = L.ix.X[(int64_t)u * L.ix.npad + it.qbeg];
-                uhi = L.ix.X[(int64_t)u * L.ix.npad + it.qbeg + it.qlen - 1];
+                const double *Uq = asym ? L.ix.XQ + (int64_t)u * L.ix.qnpad : L.ix.X + (int64_t)u * L.ix.npad;
+                ulo = Uq[it.qbeg];
+                uhi = Uq[it.qbeg + it.qlen - 1];
             }
             // Tile packing runs in lane 0 alone: the open tile [cr0, cr0 + TC_N),
             // its valid-row mask cm, the tile waiting to be pushed (pend) and
@@ -631,7 +647,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
                 int64_t ws = 0, we = 0;
                 if (nb0 + lane < nb_end) {
                     const uint32_t b = L.ix.adj[nb0 + lane];
-                    if (b == it.cell) {
+                    if (!asym && b == it.cell) {
                         ws = it.qbeg;
                         we = cell_end;
                     } else {
@@ -861,8 +877,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
                         const unsigned same = __ballot_sync(0xffffffffu, (uint32_t)lane < n && S.rq_j[w][pos + lane] == j0);
                         n = (same == 0xffffffffu) ? 32u : (uint32_t)(__ffs(~same) - 1);
                         unsigned long long c = 0;
-                        tc_flush_survivors(&T, &S.rq_q[w][pos], &S.rq_c[w][pos], n, nullptr, nullptr, nullptr, &c, j0,
-                                           dpos);
+                        tc_flush_survivors<ASYM>(&T, &S.rq_q[w][pos], &S.rq_c[w][pos], n, nullptr, nullptr, nullptr,
+                                                 &c, j0, dpos);
                         counted += c;
                         head[w] += n;
                         __syncwarp();
@@ -912,7 +928,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
         auto flush = [&]() {
             unsigned long long c = 0;
             __syncwarp();
-            tc_flush_survivors(&T, sq, sc, nq, nullptr, nullptr, nullptr, &c, it_job, dpos);
+            tc_flush_survivors<ASYM>(&T, sq, sc, nq, nullptr, nullptr, nullptr, &c, it_job, dpos);
             __syncwarp();
             counted += c;
             nq = 0;
@@ -994,17 +1010,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
                 it_job = new_job;
             }
             if (anyhit) {
-                // this lane's survivors: marked columns with cpos >= qpos (one
-                // orientation; rows of the other searched cells lie after the
-                // query cell)
+                // this lane's survivors: marked columns, in a self-join those
+                // with cpos >= qpos (one orientation; rows of the other
+                // searched cells lie after the query cell)
                 uint32_t k = 0;
+                const bool sym = !ASYM;
 #pragma unroll
                 for (int c = 0; c < 8; ++c) {
                     const uint32_t col0 = r0 + (uint32_t)c * 32u;
-                    if (col0 + 31u < it_qpos)
-                        hm[c] = 0u;
-                    else if (col0 < it_qpos)
-                        hm[c] &= ~((1u << (it_qpos - col0)) - 1u);
+                    if (sym) {
+                        if (col0 + 31u < it_qpos)
+                            hm[c] = 0u;
+                        else if (col0 < it_qpos)
+                            hm[c] &= ~((1u << (it_qpos - col0)) - 1u);
+                    }
                     k += (uint32_t)__popc(hm[c]);
                 }
                 uint32_t incl = k;
@@ -1045,7 +1064,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
 #pragma unroll
                         for (int c = 0; c < 8; ++c)
                             if (__any_sync(0xffffffffu, hm[c] != 0u))
-                                nq = tc_queue_bits(&T, hm[c], (uint32_t)c * 32u, it_qpos, r0, sq, sc, nq, nullptr,
+                                nq = tc_queue_bits<ASYM>(&T, hm[c], (uint32_t)c * 32u, it_qpos, r0, sq, sc, nq, nullptr,
                                                    nullptr, nullptr, surv_w, &S.counted, it_job, dpos);
                     }
                 }
@@ -1198,21 +1217,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
             if (anyhit) {
                 const uint32_t cb = (uint32_t)hh * 128u;
                 if (__any_sync(0xffffffffu, hm0 != 0u))
-                    nq = tc_queue_bits(&T, hm0, cb + 0u, qpos, r0, sq, sc, nq, stg, &S.cnt[half],
+                    nq = tc_queue_bits<ASYM>(&T, hm0, cb + 0u, qpos, r0, sq, sc, nq, stg, &S.cnt[half],
                                        &S.flush_req, surv_w, &S.counted, it_job);
                 if (__any_sync(0xffffffffu, hm1 != 0u))
-                    nq = tc_queue_bits(&T, hm1, cb + 32u, qpos, r0, sq, sc, nq, stg, &S.cnt[half],
+                    nq = tc_queue_bits<ASYM>(&T, hm1, cb + 32u, qpos, r0, sq, sc, nq, stg, &S.cnt[half],
                                        &S.flush_req, surv_w, &S.counted, it_job);
                 if (__any_sync(0xffffffffu, hm2 != 0u))
-                    nq = tc_queue_bits(&T, hm2, cb + 64u, qpos, r0, sq, sc, nq, stg, &S.cnt[half],
+                    nq = tc_queue_bits<ASYM>(&T, hm2, cb + 64u, qpos, r0, sq, sc, nq, stg, &S.cnt[half],
                                        &S.flush_req, surv_w, &S.counted, it_job);
                 if (__any_sync(0xffffffffu, hm3 != 0u))
-                    nq = tc_queue_bits(&T, hm3, cb + 96u, qpos, r0, sq, sc, nq, stg, &S.cnt[half],
+                    nq = tc_queue_bits<ASYM>(&T, hm3, cb + 96u, qpos, r0, sq, sc, nq, stg, &S.cnt[half],
                                        &S.flush_req, surv_w, &S.counted, it_job);
                 if (early && nq) {
                     unsigned long long c = 0;
                     __syncwarp();
-                    tc_flush_survivors(&T, sq, sc, nq, stg, &S.cnt[half], &S.flush_req, &c, it_job);
+                    tc_flush_survivors<ASYM>(&T, sq, sc, nq, stg, &S.cnt[half], &S.flush_req, &c, it_job);
                     __syncwarp();
                     if (c)
                         atomicAdd(&S.counted, c);
@@ -1234,7 +1253,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
             if (nq >= 32u || ((item_end || flush || (flags & F_TERM)) && nq)) {
                 unsigned long long c = 0;
                 __syncwarp();
-                tc_flush_survivors(&T, sq, sc, nq, stg, &S.cnt[half], &S.flush_req, &c, it_job);
+                tc_flush_survivors<ASYM>(&T, sq, sc, nq, stg, &S.cnt[half], &S.flush_req, &c, it_job);
                 __syncwarp();
                 if (c)
                     atomicAdd(&S.counted, c);
@@ -1362,6 +1381,7 @@ __device__ __forceinline__ __half tc_coord(const double *__restrict__ X, int64_t
 }
 
 // XA/XB: row p at core matrix ((p/8)*(Kp/8) + k/8), row p%8, element k%8.
+// Either may be null (Q join_eps E packs its queries as A rows only).
 __global__ void k_tc_pack(const double *__restrict__ X, int64_t n, int64_t npad, TcPrepParams P,
                           uint4 *__restrict__ XA, uint4 *__restrict__ XB)
 {
@@ -1404,8 +1424,10 @@ __global__ void k_tc_pack(const double *__restrict__ X, int64_t n, int64_t npad,
         }
         const int64_t r = p + P.row_off;
         const int64_t idx = ((r >> 3) * (Kp / 8) + kc) * 8 + (r & 7);   // in 16-byte units
-        XA[idx] = *reinterpret_cast<const uint4 *>(a);
-        XB[idx] = *reinterpret_cast<const uint4 *>(b);
+        if (XA)
+            XA[idx] = *reinterpret_cast<const uint4 *>(a);
+        if (XB)
+            XB[idx] = *reinterpret_cast<const uint4 *>(b);
     }
 }
 
@@ -1434,31 +1456,13 @@ int tc_prepare(gj_index *h, const double *stats_host, const int *perm, cudaStrea
     for (int j = 0; j < d; ++j)
         c[j] = 0.5 * (stats_host[(size_t)perm[j] * 4 + 2] + stats_host[(size_t)perm[j] * 4 + 3]);
     double *centre = nullptr;
-    unsigned long long *rmax = nullptr;
     cudaError_t e = dev_alloc(&centre, d * sizeof(double), s);
     if (e == cudaSuccess)
-        e = dev_alloc(&rmax, sizeof(unsigned long long), s);
-    if (e == cudaSuccess)
         e = cudaMemcpyAsync(centre, c.data(), d * sizeof(double), cudaMemcpyHostToDevice, s);
+    double R0 = 0.0;
     if (e == cudaSuccess)
-        e = cudaMemsetAsync(rmax, 0, sizeof(unsigned long long), s);
-    unsigned long long rbits = 0;
-    if (e == cudaSuccess) {
-        note_launch();
-        k_tc_radius<<<(int)((n + 255) / 256), 256, 0, s>>>(h->X, n, h->npad, d, centre, rmax);
-        e = cudaGetLastError();
-    }
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(&rbits, rmax, sizeof(rbits), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess)
-        e = cudaStreamSynchronize(s);
-    double R2 = 0.0;
-    memcpy(&R2, &rbits, sizeof(R2));
-    const double R0 = sqrt(R2) * (1.0 + ldexp(1.0, -30));
-    int sexp = 0;
-    if (R0 > 0.0)
-        sexp = (int)floor(log2(250.0 / R0));
-    const double sigma = ldexp(1.0, sexp);
+        e = tc_radius(h->X, n, h->npad, d, centre, &R0, s);
+    const double sigma = tc_sigma_for(R0);
     const int64_t rows = h->npad + 512;
     const size_t bytes = (size_t)rows * Kp * 2;
     if (e == cudaSuccess)
@@ -1475,8 +1479,7 @@ int tc_prepare(gj_index *h, const double *stats_host, const int *perm, cudaStrea
         k_tc_pack<<<(int)((n + 127) / 128), 128, 0, s>>>(h->X, n, h->npad, P, (uint4 *)h->XA, (uint4 *)h->XB);
         e = cudaGetLastError();
     }
-    h->tc_centre = centre;   // kept: a many-jobs layout re-packs from it
-    dev_free(rmax, s);
+    h->tc_centre = centre;   // kept: a many-jobs layout and Q join_eps E re-pack from it
     if (e != cudaSuccess)
         return e == cudaErrorMemoryAllocation ? GJ_ERR_OOM : GJ_ERR_CUDA;
     const double Td = tc_threshold(h->info.eps, sigma, R0, d, Kp);
@@ -1541,7 +1544,7 @@ cudaError_t tc_jobs_launch_attr(int Kp)
     size_t sm = 0;
     if (tc_stages(Kp, &a, &b, &ob, &os, &sm) < 2)
         return cudaErrorInvalidValue;
-    return cudaFuncSetAttribute(k_join_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    return cudaFuncSetAttribute(k_join_tc<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
 }
 
 // (call tc_jobs_launch_attr first: this launcher sets no attribute, so it can
@@ -1563,7 +1566,7 @@ cudaError_t launch_join_tc_jobs(const JoinLaunch &L, const void *XA, const void 
     T.NS = tc_stages(T.Kp, &T.a_bytes, &T.b_bytes, &T.off_b, &T.off_s, &sm);
     if (T.NS < 2)
         return cudaErrorInvalidValue;
-    k_join_tc<true><<<grid, TC_THREADS, sm, s>>>(T);   // every job writes its own buffer directly
+    k_join_tc<true, false><<<grid, TC_THREADS, sm, s>>>(T);   // every job writes its own buffer directly
     return cudaGetLastError();
 }
 
@@ -1580,16 +1583,80 @@ cudaError_t launch_join_tc(const gj_index *h, const JoinLaunch &L, int grid, cud
     T.NS = tc_stages(T.Kp, &T.a_bytes, &T.b_bytes, &T.off_b, &T.off_s, &sm);
     if (T.NS < 2)
         return cudaErrorInvalidValue;
-    cudaError_t e = direct ? cudaFuncSetAttribute(k_join_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)
-                           : cudaFuncSetAttribute(k_join_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = direct
+                        ? cudaFuncSetAttribute(k_join_tc<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)
+                        : cudaFuncSetAttribute(k_join_tc<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)sm);
     if (e != cudaSuccess)
         return e;
     note_launch();
     if (direct)
-        k_join_tc<true><<<grid, TC_THREADS, sm, s>>>(T);
+        k_join_tc<true, false><<<grid, TC_THREADS, sm, s>>>(T);
     else
-        k_join_tc<false><<<grid, TC_THREADS, sm, s>>>(T);
+        k_join_tc<false, false><<<grid, TC_THREADS, sm, s>>>(T);
     return cudaGetLastError();
+}
+
+// Direct form over explicit operand arrays and threshold (Q join_eps E: query
+// A rows, entry B rows, both under one centre and scale).
+cudaError_t launch_join_tc_ops(const JoinLaunch &L, const void *XA, const void *XB, int Kp, int Tbits, int grid,
+                               cudaStream_t s)
+{
+    TcLaunch T{};
+    T.J = L;
+    T.XA = (const unsigned char *)XA;
+    T.XB = (const unsigned char *)XB;
+    T.Kp = Kp;
+    T.Tbits = Tbits;
+    T.limit_ns = wait_limit_ns();
+    size_t sm = 0;
+    T.NS = tc_stages(T.Kp, &T.a_bytes, &T.b_bytes, &T.off_b, &T.off_s, &sm);
+    if (T.NS < 2)
+        return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(k_join_tc<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess)
+        return e;
+    note_launch();
+    k_join_tc<true, true><<<grid, TC_THREADS, sm, s>>>(T);
+    return cudaGetLastError();
+}
+
+// Radius of a point set about a centre: sqrt of the largest squared distance
+// (times 1 + 2^-30, the same widening as the index build's).
+cudaError_t tc_radius(const double *X, int64_t n, int64_t npad, int d, const double *centre, double *R0,
+                      cudaStream_t s)
+{
+    *R0 = 0.0;
+    if (n <= 0)
+        return cudaSuccess;
+    unsigned long long *rmax = nullptr;
+    unsigned long long rbits = 0;
+    cudaError_t e = dev_alloc(&rmax, sizeof(unsigned long long), s);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(rmax, 0, sizeof(unsigned long long), s);
+    if (e == cudaSuccess) {
+        note_launch();
+        k_tc_radius<<<(int)((n + 255) / 256), 256, 0, s>>>(X, n, npad, d, centre, rmax);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&rbits, rmax, sizeof(rbits), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(s);
+    dev_free(rmax, s);
+    double R2 = 0.0;
+    memcpy(&R2, &rbits, sizeof(R2));
+    *R0 = sqrt(R2) * (1.0 + ldexp(1.0, -30));
+    return e;
+}
+
+// The power-of-two scale that keeps every |h| of a set of radius R0 at most 250.
+double tc_sigma_for(double R0)
+{
+    int sexp = 0;
+    if (R0 > 0.0)
+        sexp = (int)floor(log2(250.0 / R0));
+    return ldexp(1.0, sexp);
 }
 
 // ---------------------------------------------------------------------------

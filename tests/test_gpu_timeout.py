@@ -59,3 +59,25 @@ def test_wait_expiry_reports_timeout_and_the_context_stays_usable():
         assert st == gj.GJ_OK and m == n and np.array_equal(keys(host[:m]), ref)
     with gj.Index(X, eps, k=1, flags=TC) as it2:           # and a new index on the same context
         assert np.array_equal(keys(it2.join()), ref)
+
+
+def test_wait_expiry_in_the_tensor_core_similarity_join():
+    E = synth.uniform(20_000, 16, 73)
+    Q = synth.uniform(5_000, 16, 74)
+    eps = 0.45
+    with gj.Index(E, eps, k=1) as ip:
+        st, m = gj.gj_join_qe(ip.h, Q, None)
+        assert st == gj.GJ_OK
+        ref = keys(ip.join_qe(Q))
+    with gj.Index(E, eps, k=1, flags=TC) as it:
+        out = torch.empty((m + 8, 2), dtype=torch.int32, device="cuda")
+        try:
+            gj.gj_debug_set_wait_limit(1)
+            st, _ = gj.gj_join_qe(it.h, torch.from_numpy(Q).cuda(), out)
+            assert st == gj.GJ_ERR_TIMEOUT
+        finally:
+            gj.gj_debug_set_wait_limit(0)
+        torch.cuda.synchronize()
+        st, m2 = gj.gj_join_qe(it.h, Q, out)
+        assert st == gj.GJ_OK and m2 == m
+        assert np.array_equal(keys(out[:m].cpu().numpy().view(np.uint32)), ref)
