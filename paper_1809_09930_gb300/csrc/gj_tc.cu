@@ -18,24 +18,27 @@
 // accumulation (taken as <= (K+2) * 2^-22 * sum of |terms|, twice a
 // truncating adder's bound).  Every pair of R therefore survives.
 //
-// Kernel (one persistent CTA per SM, 320 threads):
-//   warp 0   producer: takes work items (query blocks of <= 120 points),
+// Kernel (one persistent CTA per SM, 384 threads):
+//   warp 0   producer: takes work items (query blocks of <= 128 points),
 //            computes the SORTIDU windows of the adjacent cells (one per lane),
 //            packs them into 256-row candidate tiles under a valid-row mask
-//            (lane 0 alone, state in registers; whole tiles of a long window
-//            take a short path), loads the item's 128-row A tile and each
-//            candidate tile with bulk asynchronous copies (TMA) into a ring of
-//            shared-memory stages, and passes tile descriptors down a ring;
-//   warp 1   one thread issues tcgen05.mma (one M=128 x N=256 MMA per K step)
-//            into a double-buffered TMEM accumulator (2 x 256 fp32 columns)
-//            and commits to mbarriers;
-//   warps 2-9 epilogue: read the accumulators 32 columns at a time with
+//            (lane 0, state in registers; runs of whole tiles are pushed
+//            warp-wide, one ring stage per lane), and loads the item's 128-row
+//            A tile and each candidate tile with bulk asynchronous copies into
+//            shared-memory stages, the tile descriptor beside each stage;
+//   warps 1, 10  MMA issuers, one thread each, one 256-column fp32 TMEM
+//            accumulator each (turns of parity 0 and 1): one M=128 x N=256
+//            tcgen05.mma per K step, commits to the stage's and the
+//            accumulator's mbarriers;
+//   warps 2-9 epilogue: read an accumulator 32 columns at a time with
 //            tcgen05.ld.red, which also returns each lane's minimum, mark the
 //            values <= T of a chunk whose minimum is <= T in per-lane bit
-//            masks, release the accumulator, then queue
-//            the marked candidates and recheck them in FP64 in batches; exact
-//            pairs go to a double-buffered per-CTA staging area committed to
-//            the output per item (same resume protocol as the plain kernel).
+//            masks and release the accumulator.  Direct form: two groups of
+//            four warps, one per accumulator, hand their survivors to
+//   warp 11  the recheck warp, which runs the FP64 test and writes the exact
+//            pairs straight to the output.  Staged form: all eight warps read
+//            each tile, recheck their own survivors and commit per-CTA staging
+//            per item (the plain kernel's resume protocol).
 // Every wait is bounded (globaltimer); on timeout the CTA flags the error,
 // lets in-flight copies land, frees its TMEM and returns.
 #include <cuda_fp16.h>
