@@ -96,7 +96,9 @@ struct alignas(16) TileDesc {
 struct TcShared {
     uint64_t full_b[8], empty_b[8];
     uint64_t full_a[2], empty_a[2];
-    uint64_t tmem_full[2], tmem_empty[2], desc_full[2];
+    // tmem_full: two arrivals per use, the MMA issuer's once the tile's
+    // descriptor is written (release) and its commit once the MMAs land
+    uint64_t tmem_full[2], tmem_empty[2];
     uint64_t epi_bar[2];
     uint64_t fin[2];         // per MMA issuer: its last commit has landed
     // the descriptor of a stage's current turn: the MMA issuer copies it
@@ -385,9 +387,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
         for (int i = 0; i < 2; ++i) {
             mbar_init(&S.full_a[i], 1);
             mbar_init(&S.empty_a[i], 2);   // both MMA issuers commit at the item's end
-            mbar_init(&S.tmem_full[i], 1);
-            mbar_init(&S.tmem_empty[i], DIRECT ? 4 : 8);   // the warps that read the accumulator
-            mbar_init(&S.desc_full[i], 1);
+            mbar_init(&S.tmem_full[i], 2);
+            mbar_init(&S.tmem_empty[i], 8);   // the eight epilogue warps read every accumulator
             mbar_init(&S.epi_bar[i], 8);
             mbar_init(&S.fin[i], 1);
         }
@@ -822,11 +823,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
                     for (int ks = 1; ks < ksteps; ++ks)
                         mma_f16(dcol, ad + (uint64_t)(ks * 16), bd + (uint64_t)(ks * 16), idesc, 1u);
                     mma_commit(&S.empty_b[stage]);
-                    mbar_arrive(&S.desc_full[acc]);
-                    mma_commit(&S.tmem_full[acc]);
+                    mbar_arrive(&S.tmem_full[acc]);   // the descriptor
+                    mma_commit(&S.tmem_full[acc]);    // the accumulator
                 } else {
                     mbar_arrive(&S.empty_b[stage]);
-                    mbar_arrive(&S.desc_full[acc]);
+                    mbar_arrive(&S.tmem_full[acc]);
                     mbar_arrive(&S.tmem_full[acc]);
                 }
                 if (flags & F_TERM)
@@ -906,13 +907,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
         }
     } else if constexpr (DIRECT) {
         // ------------------------------------------------------------ epilogue (direct output)
-        // Group g (warps 2-5: g = 0, warps 6-9: g = 1) takes the turns of
-        // parity g from accumulator g; each warp reads its 32 rows (its TMEM
-        // lane quadrant) across all 256 columns.  While one group scans its
-        // tile the other waits for, or scans, the next: two tiles are in the
-        // epilogue at once.
-        const int e = warp - 2, q = warp & 3;
-        const uint32_t g = (uint32_t)(e >> 2);
+        // All eight warps take every turn: warp e reads its 32 rows (TMEM
+        // lane quadrant q) in the column half hh of the turn's accumulator,
+        // two rounds of two 32-column loads, so a tile is read in half the
+        // time one warp per quadrant would take; meanwhile the other
+        // accumulator is refilled.  The warps never agree on anything: each
+        // releases its share of the accumulator and queues its own hits.
+        const int e = warp - 2, q = warp & 3, hh = e >> 2;
         uint32_t *const sq = S.sq[e], *const sc = S.sc[e];
         uint32_t nq = 0;
         const float Tf0 = __int_as_float(T.Tbits);
@@ -927,7 +928,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
         uint32_t rq_tail = 0;                // this warp's ring: positions written
         bool dead = false;
         long long t_job = clock64();
-        const bool lead = (e & 3) == 0 && lane == 0;   // one lane per group (tuning launches)
+        const bool lead = e == 0 && lane == 0;   // one lane of the epilogue (tuning launches)
         auto flush = [&]() {
             unsigned long long c = 0;
             __syncwarp();
@@ -936,17 +937,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
             counted += c;
             nq = 0;
         };
-        for (uint32_t use = 0;; ++use) {
-            const uint32_t par = use & 1u;
-            const bool ok = mbar_wait(&S.desc_full[g], par, abort, T.limit_ns) &&
-                            mbar_wait(&S.tmem_full[g], par, abort, T.limit_ns);
+        for (uint32_t turn = 0;; ++turn) {
+            const uint32_t acc = turn & 1u, par = (turn >> 1) & 1u;
+            const bool ok = mbar_wait(&S.tmem_full[acc], par, abort, T.limit_ns);
             // one decision per warp: the TMEM loads below need all 32 lanes
             if (__any_sync(0xffffffffu, !ok)) {
                 dead = true;
                 break;
             }
             tc_fence_after();
-            const TileDesc *Dp = &S.tdesc[g];
+            const TileDesc *Dp = &S.tdesc[acc];
             const uint32_t flags = Dp->flags;
             if (flags & F_TERM)
                 break;
@@ -961,18 +961,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
                 new_job = Dp->p2;
                 it_Tf = T.jobs ? __uint_as_float(Dp->p3) : Tf0;
             }
-            uint32_t hm[8];
+            uint32_t hm[4];   // this lane's hits in the 4 chunks of its column half
 #pragma unroll
-            for (int c = 0; c < 8; ++c)
+            for (int c = 0; c < 4; ++c)
                 hm[c] = 0u;
             bool anyhit = false;
             uint32_t r0 = 0;
+            const uint32_t cb = (uint32_t)hh * 128u;
             if (!(flags & F_MARKER)) {
                 const float Tf = it_Tf;
                 const bool rvalid = it_rvalid;
-                const uint32_t tb = tmem + ((uint32_t)(q * 32) << 16) + g * 256u;
+                const uint32_t tb = tmem + ((uint32_t)(q * 32) << 16) + acc * 256u + cb;
 #pragma unroll
-                for (int rd = 0; rd < 4; ++rd) {
+                for (int rd = 0; rd < 2; ++rd) {
                     uint32_t va[32], vb[32];
                     float ma, mb;
                     tmem_ld32_min(tb + rd * 64u, va, ma);
@@ -981,7 +982,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
                     const bool ha = rvalid && ma <= Tf, hb = rvalid && mb <= Tf;
                     if (__any_sync(0xffffffffu, ha || hb)) {
                         // valid rows of the tile: read only for a chunk with hits
-                        const uint32_t *vmp = Dp->mask + rd * 2;
+                        const uint32_t *vmp = Dp->mask + hh * 4 + rd * 2;
                         anyhit = true;
                         if (ha)
                             hm[rd * 2 + 0] = hit_mask32(va, Tf) & vmp[0];
@@ -992,11 +993,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
                 if (anyhit)
                     r0 = Dp->r0;
             }
-            // release the accumulator (and with it the descriptor slot)
+            // release this warp's share of the accumulator (and with the last
+            // share the descriptor slot)
             tc_fence_before();
             __syncwarp();
             if (lane == 0)
-                mbar_arrive(&S.tmem_empty[g]);
+                mbar_arrive(&S.tmem_empty[acc]);
             // reconverge: otherwise lanes 1-31 run ahead into the next wait's
             // polling loop and lane 0's remaining work interleaves with it
             __syncwarp();
@@ -1019,8 +1021,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
                 uint32_t k = 0;
                 const bool sym = !ASYM;
 #pragma unroll
-                for (int c = 0; c < 8; ++c) {
-                    const uint32_t col0 = r0 + (uint32_t)c * 32u;
+                for (int c = 0; c < 4; ++c) {
+                    const uint32_t col0 = r0 + cb + (uint32_t)c * 32u;
                     if (sym) {
                         if (col0 + 31u < it_qpos)
                             hm[c] = 0u;
@@ -1042,14 +1044,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
                         // room in the ring: hand them to the recheck warp
                         uint32_t at = rq_tail + incl - k;
 #pragma unroll
-                        for (int c = 0; c < 8; ++c) {
+                        for (int c = 0; c < 4; ++c) {
                             uint32_t mm = hm[c];
                             while (mm) {
                                 const uint32_t b = (uint32_t)(__ffs(mm) - 1);
                                 mm &= mm - 1u;
                                 const uint32_t slot = at & (uint32_t)(TC_RQ - 1);
                                 S.rq_q[e][slot] = it_qpos;
-                                S.rq_c[e][slot] = r0 + (uint32_t)c * 32u + b;
+                                S.rq_c[e][slot] = r0 + cb + (uint32_t)c * 32u + b;
                                 S.rq_j[e][slot] = it_job;
                                 ++at;
                             }
@@ -1065,9 +1067,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
                     } else {
                         // ring full (dense data): recheck them here
 #pragma unroll
-                        for (int c = 0; c < 8; ++c)
+                        for (int c = 0; c < 4; ++c)
                             if (__any_sync(0xffffffffu, hm[c] != 0u))
-                                nq = tc_queue_bits<ASYM>(&T, hm[c], (uint32_t)c * 32u, it_qpos, r0, sq, sc, nq, nullptr,
+                                nq = tc_queue_bits<ASYM>(&T, hm[c], cb + (uint32_t)c * 32u, it_qpos, r0, sq, sc, nq, nullptr,
                                                    nullptr, nullptr, surv_w, &S.counted, it_job, dpos);
                     }
                 }
@@ -1131,8 +1133,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
         };
         for (;;) {
             const uint32_t acc = turn & 1u, par = (turn >> 1) & 1u;
-            const bool ok = mbar_wait(&S.desc_full[acc], par, abort, T.limit_ns) &&
-                            mbar_wait(&S.tmem_full[acc], par, abort, T.limit_ns);
+            const bool ok = mbar_wait(&S.tmem_full[acc], par, abort, T.limit_ns);
             // one decision per warp: the TMEM loads below need all 32 lanes
             if (__any_sync(0xffffffffu, !ok)) {
                 dead = true;
