@@ -30,15 +30,16 @@
 //            accumulator each (turns of parity 0 and 1): one M=128 x N=256
 //            tcgen05.mma per K step, commits to the stage's and the
 //            accumulator's mbarriers;
-//   warps 2-9 epilogue: read an accumulator 32 columns at a time with
-//            tcgen05.ld.red, which also returns each lane's minimum, mark the
-//            values <= T of a chunk whose minimum is <= T in per-lane bit
-//            masks and release the accumulator.  Direct form: two groups of
-//            four warps, one per accumulator, hand their survivors to
+//   warps 2-9 epilogue: every warp reads its 32 TMEM lanes of one 128-column
+//            half of each tile, 32 columns at a time with tcgen05.ld.red,
+//            which also returns each lane's minimum, marks the values <= T of
+//            a chunk whose minimum is <= T in per-lane bit masks and releases
+//            its share of the accumulator.  Direct form: the warps hand their
+//            survivors to
 //   warp 11  the recheck warp, which runs the FP64 test and writes the exact
-//            pairs straight to the output.  Staged form: all eight warps read
-//            each tile, recheck their own survivors and commit per-CTA staging
-//            per item (the plain kernel's resume protocol).
+//            pairs straight to the output.  Staged form: the warps recheck
+//            their own survivors and commit per-CTA staging per item (the
+//            plain kernel's resume protocol).
 // Every wait is bounded (globaltimer); on timeout the CTA flags the error,
 // lets in-flight copies land, frees its TMEM and returns.
 #include <cuda_fp16.h>
@@ -363,9 +364,8 @@ __device__ __forceinline__ uint32_t tc_queue_bits(const TcLaunch *__restrict__ T
 // DIRECT = false: output through per-CTA staging committed per work item
 // (exact resume; result batches for host output).  DIRECT = true: pairs go
 // straight to the output (or a many-jobs launch's job buffers) with one
-// reservation per warp, so the epilogue needs no agreement between warps and
-// runs as two groups of four warps, one per accumulator, that work on
-// alternate tiles.
+// reservation per warp, so the epilogue warps never agree on anything: each
+// reads its share of every tile and moves on.
 template <bool DIRECT, bool ASYM>
 __global__ void __launch_bounds__(TC_THREADS, 1) k_join_tc(const TcLaunch T)
 {
