@@ -149,3 +149,50 @@ def test_threshold_argument_checks():
     assert gj.gj_tc_threshold(0.1, 1.0, 1.0, 0)[0] == gj.GJ_ERR_INVALID_ARG
     assert gj.gj_tc_threshold(0.1, 1.0, 1.0, 125)[0] == gj.GJ_ERR_INVALID_ARG
     assert gj.gj_tc_threshold(0.1, 1.0, 1.0, 124)[0] == gj.GJ_OK
+
+
+def test_qe_packing_covers_queries_beyond_the_entries():
+    """Q join_eps E packs queries and entries under the entries' centre with one
+    scale and one radius bound taken over both sets.  Queries a full eps
+    outside the entries' ball, each with a partner just inside eps: every
+    query-entry pair within eps must give t <= T in any accumulation order.
+    With the entries' own scale and radius the same pairs fail (the query
+    norms overflow fp16, or exceed the margin), so the wider choice is needed."""
+    rng = np.random.default_rng(17)
+    d = 16
+    E = synth.uniform(600, d, 5)
+    c, R0e, sigma_e = _scale(E)
+    eps = 0.6 * R0e
+    far = np.argsort(-((E - c) ** 2).sum(axis=1))[:150]
+    out = (E[far] - c) / np.linalg.norm(E[far] - c, axis=1, keepdims=True)
+    jitter = rng.standard_normal((150, d)) * 0.05
+    u = out + jitter
+    u /= np.linalg.norm(u, axis=1, keepdims=True)
+    Q = np.vstack([E[far] + eps * (1 - 1e-12) * u, synth.uniform(100, d, 6)])
+    R0q = float(np.sqrt(((Q - c) ** 2).sum(axis=1).max())) * (1 + 2.0 ** -30)
+    assert R0q > R0e * 1.4
+    R0 = max(R0e, R0q)
+    sigma = 2.0 ** np.floor(np.log2(250.0 / R0))
+    s = ((Q[:, None, :] - E[None, :, :]) ** 2).sum(axis=2)
+    i, j = np.nonzero(s <= eps * eps)
+    assert len(i) >= 150
+    st, T = gj.gj_tc_threshold(eps, sigma, R0, d)
+    assert st == gj.GJ_OK
+    A, _ = _operands(Q, c, sigma)
+    _, B = _operands(E, c, sigma)
+    P = A[i] * B[j]
+    assert np.all(P.astype(np.float32).astype(np.float64) == P)
+    K = P.shape[1]
+    Tf = np.float32(T)
+    for order in (list(range(K)), list(range(K))[::-1], list(range(d, K)) + list(range(d))):
+        for mode in ("rn", "rz"):
+            assert np.all(_accumulate(P, order, mode) <= Tf)
+    assert np.all(_accumulate(P, list(range(K)), "tree") <= Tf)
+    # the entries' own packing loses pairs
+    st, Te = gj.gj_tc_threshold(eps, sigma_e, R0e, d)
+    assert st == gj.GJ_OK
+    with np.errstate(over="ignore", invalid="ignore"):
+        Ae, _ = _operands(Q, c, sigma_e)
+        _, Be = _operands(E, c, sigma_e)
+        te = _accumulate(Ae[i] * Be[j], list(range(K)), "rn")
+    assert not np.all(te <= np.float32(Te))
