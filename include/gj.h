@@ -204,7 +204,11 @@ int gj_autotune(const double *points, int64_t n, int32_t d, double eps, const gj
  * GJ_TC_FILTER (and without GJ_HOST_BATCHED) the join runs in one pass into a
  * device buffer of cap pairs from the stream-ordered pool, copied to
  * pairs_out when the join ends; it falls back to the result batches when that
- * buffer cannot be allocated.
+ * buffer cannot be allocated.  Memory: the first join on a handle allocates
+ * its launch state (control block, pinned mirrors, work order, deferred
+ * lists, events), which the handle keeps until gj_free; the per-call buffers
+ * (staging, result batches, the tensor-core output buffer) come from the
+ * device's stream-ordered pool, which keeps freed blocks for reuse.
  */
 int gj_self_join(gj_index *h, gj_pair *pairs_out, uint64_t cap, uint64_t *count);
 
@@ -269,11 +273,11 @@ int gj_neighbor_table(gj_index *h, int64_t *row_start, uint32_t *nbr, uint64_t c
 
 /*
  * A self-join that allocates nothing (no paper counterpart).  gj_self_join
- * allocates its launch state (control block, work order, deferred lists,
- * staging) with cudaMalloc on every call.  Callers whose device memory is
- * reserved up front by a caching allocator, or whose latency budget forbids
- * entering the driver's allocator during a join, cannot accept that; this entry
- * point serves them.  It runs the plain FP64 join (not the tensor-core filter)
+ * allocates its launch state on a handle's first join and takes its staging
+ * and batch buffers from the stream-ordered pool on every call.  Callers whose
+ * device memory is reserved up front by a caching allocator, or whose latency
+ * budget forbids entering the driver's allocator during a join, cannot accept
+ * that; this entry point serves them.  It runs the plain FP64 join (not the tensor-core filter)
  * and writes pairs straight into pairs_out, which must be device memory of the
  * handle's device, else GJ_ERR_INVALID_ARG (NULL with cap == 0: count only; a
  * non-NULL pairs_out with cap == 0 writes nothing and returns GJ_ERR_CAPACITY

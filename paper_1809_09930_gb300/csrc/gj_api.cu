@@ -130,25 +130,28 @@ double now_ms()
     return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
-struct JoinBuffers {
+}  // namespace
+
+namespace gj {
+
+// Launch state of the staged join whose sizes are fixed per handle (the grid
+// and the work items are): allocated by the first staged join and kept until
+// gj_free, so later joins allocate no pinned memory and create no events.
+struct StagedState {
     JoinCtl *ctl = nullptr;
     JoinCtl *hctl_up = nullptr, *hctl_dn = nullptr;   // pinned
     Deferred *def[2] = {nullptr, nullptr};
-    gj_pair *staging = nullptr;
-    gj_pair *dbuf[2] = {nullptr, nullptr};
-    uint32_t *queue = nullptr, *qtmp = nullptr, *sample = nullptr;
+    uint32_t dcap = 0;                                 // entries of each deferred list
+    uint32_t *queue = nullptr, *qtmp = nullptr, *sample = nullptr;   // one entry per work item
     unsigned long long *span = nullptr, *hspan = nullptr;   // per-SM spans (device, pinned host)
     cudaEvent_t ev_k0 = nullptr, ev_k1 = nullptr, ev_ctl = nullptr, ev_drained[2] = {nullptr, nullptr};
-    ~JoinBuffers()
+    ~StagedState()
     {
         cudaFree(ctl);
         cudaFreeHost(hctl_up);
         cudaFreeHost(hctl_dn);
         cudaFree(def[0]);
         cudaFree(def[1]);
-        cudaFree(staging);
-        cudaFree(dbuf[0]);
-        cudaFree(dbuf[1]);
         cudaFree(queue);
         cudaFree(qtmp);
         cudaFree(sample);
@@ -161,6 +164,84 @@ struct JoinBuffers {
             if (e) cudaEventDestroy(e);
     }
 };
+
+}  // namespace gj
+
+namespace {
+
+// One staged join's buffers: the handle's StagedState, borrowed, and the
+// buffers whose sizes depend on the call (staging, result batches), taken from
+// the stream-ordered pool and returned when the join ends.
+struct JoinBuffers {
+    JoinCtl *ctl = nullptr;
+    JoinCtl *hctl_up = nullptr, *hctl_dn = nullptr;
+    Deferred *def[2] = {nullptr, nullptr};
+    uint32_t *queue = nullptr, *qtmp = nullptr, *sample = nullptr;
+    unsigned long long *span = nullptr, *hspan = nullptr;
+    cudaEvent_t ev_k0 = nullptr, ev_k1 = nullptr, ev_ctl = nullptr, ev_drained[2] = {nullptr, nullptr};
+    gj_pair *staging = nullptr;
+    gj_pair *dbuf[2] = {nullptr, nullptr};
+    cudaStream_t s = nullptr, drain = nullptr;
+    ~JoinBuffers()
+    {
+        // (a result batch may still be draining after an error)
+        if (drain)
+            cudaStreamSynchronize(drain);
+        dev_free(staging, s);
+        dev_free(dbuf[0], s);
+        dev_free(dbuf[1], s);
+    }
+};
+
+// The handle's staged-join state, made on first use; B borrows it.
+cudaError_t staged_state(gj_index *h, int grid, JoinBuffers &B)
+{
+    if (!h->ss) {
+        StagedState *t = new (std::nothrow) StagedState();
+        if (!t)
+            return cudaErrorMemoryAllocation;
+        const size_t ni = (size_t)std::max<int64_t>(h->nitems, 1);
+        t->dcap = (uint32_t)grid * 8u;   // a CTA defers at most the items in its pipeline
+        cudaError_t e = cudaMalloc(&t->ctl, sizeof(JoinCtl));
+        if (e == cudaSuccess) e = cudaMallocHost(&t->hctl_up, sizeof(JoinCtl));
+        if (e == cudaSuccess) e = cudaMallocHost(&t->hctl_dn, sizeof(JoinCtl));
+        if (e == cudaSuccess) e = cudaMalloc(&t->span, 2 * kSmSlots * sizeof(unsigned long long));
+        if (e == cudaSuccess) e = cudaMallocHost(&t->hspan, 2 * kSmSlots * sizeof(unsigned long long));
+        if (e == cudaSuccess) e = cudaMalloc(&t->def[0], (size_t)t->dcap * sizeof(Deferred));
+        if (e == cudaSuccess) e = cudaMalloc(&t->def[1], (size_t)t->dcap * sizeof(Deferred));
+        if (e == cudaSuccess) e = cudaMalloc(&t->queue, ni * sizeof(uint32_t));
+        if (e == cudaSuccess) e = cudaMalloc(&t->qtmp, ni * sizeof(uint32_t));
+        if (e == cudaSuccess) e = cudaMalloc(&t->sample, ni * sizeof(uint32_t));
+        if (e == cudaSuccess) e = cudaEventCreate(&t->ev_k0);
+        if (e == cudaSuccess) e = cudaEventCreate(&t->ev_k1);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&t->ev_ctl, cudaEventBlockingSync);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&t->ev_drained[0], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&t->ev_drained[1], cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            delete t;
+            return e;
+        }
+        h->ss = t;
+    }
+    const StagedState &t = *h->ss;
+    B.ctl = t.ctl;
+    B.hctl_up = t.hctl_up;
+    B.hctl_dn = t.hctl_dn;
+    B.def[0] = t.def[0];
+    B.def[1] = t.def[1];
+    B.queue = t.queue;
+    B.qtmp = t.qtmp;
+    B.sample = t.sample;
+    B.span = t.span;
+    B.hspan = t.hspan;
+    B.ev_k0 = t.ev_k0;
+    B.ev_k1 = t.ev_k1;
+    B.ev_ctl = t.ev_ctl;
+    B.ev_drained[0] = t.ev_drained[0];
+    B.ev_drained[1] = t.ev_drained[1];
+    B.s = h->stream;
+    return cudaSuccess;
+}
 
 IndexView view_of(const gj_index *h)
 {
@@ -412,22 +493,8 @@ int join_impl(gj_index *h, int part, int nparts, gj_pair *pairs_out, uint64_t ca
         if (_e != cudaSuccess)                                      \
             return cuda_status_at(_e, #x);                          \
     } while (0)
-    TRYC(cudaMalloc(&B.ctl, sizeof(JoinCtl)));
-    TRYC(cudaMallocHost(&B.hctl_up, sizeof(JoinCtl)));
-    TRYC(cudaMallocHost(&B.hctl_dn, sizeof(JoinCtl)));
-    TRYC(cudaMalloc(&B.span, 2 * kSmSlots * sizeof(unsigned long long)));
-    TRYC(cudaMallocHost(&B.hspan, 2 * kSmSlots * sizeof(unsigned long long)));
-    // a CTA defers at most the items in its pipeline when the output fills
-    const uint32_t dcap = (uint32_t)grid * 8u;
-    TRYC(cudaMalloc(&B.def[0], (size_t)dcap * sizeof(Deferred)));
-    TRYC(cudaMalloc(&B.def[1], (size_t)dcap * sizeof(Deferred)));
-    TRYC(cudaMalloc(&B.queue, nq * sizeof(uint32_t)));
-    TRYC(cudaMalloc(&B.qtmp, nq * sizeof(uint32_t)));
-    TRYC(cudaEventCreate(&B.ev_k0));
-    TRYC(cudaEventCreate(&B.ev_k1));
-    TRYC(cudaEventCreateWithFlags(&B.ev_ctl, cudaEventBlockingSync));
-    TRYC(cudaEventCreateWithFlags(&B.ev_drained[0], cudaEventDisableTiming));
-    TRYC(cudaEventCreateWithFlags(&B.ev_drained[1], cudaEventDisableTiming));
+    TRYC(staged_state(h, grid, B));
+    const uint32_t dcap = h->ss->dcap;
 
     JoinLaunch L{};
     L.ix = view_of(h);
@@ -446,10 +513,10 @@ int join_impl(gj_index *h, int part, int nparts, gj_pair *pairs_out, uint64_t ca
     const bool want_batches = !count_only_call && !dev_out;
     if (want_batches && !h->drain_stream)
         TRYC(cudaStreamCreateWithFlags(&h->drain_stream, cudaStreamNonBlocking));
+    B.drain = want_batches ? h->drain_stream : nullptr;
     const int64_t S = std::max<int64_t>(1, std::min<int64_t>(100, nq / std::max(1, grid)));
     if (want_batches && h->cfg.batch_pairs == 0 && S >= 8) {
-        const int64_t ns = (nq + S - 1) / S;
-        TRYC(cudaMalloc(&B.sample, ns * sizeof(uint32_t)));
+        const int64_t ns = (nq + S - 1) / S;   // <= nq / 8 + 1: fits the state's sample array
         note_launch();
         k_stride_queue<<<(int)((ns + 255) / 256), 256, 0, s>>>(B.qtmp, nq, S, B.sample, ns);
         TRYC(cudaGetLastError());
@@ -500,11 +567,11 @@ int join_impl(gj_index *h, int part, int nparts, gj_pair *pairs_out, uint64_t ca
     auto batch_end = [&](int64_t b) { return (b + 1) * qn + std::min<int64_t>(b + 1, rem); };
 
     if (want_batches) {
-        TRYC(cudaMalloc(&B.dbuf[0], bs * sizeof(gj_pair)));
-        TRYC(cudaMalloc(&B.dbuf[1], bs * sizeof(gj_pair)));
+        TRYC(dev_alloc(&B.dbuf[0], bs * sizeof(gj_pair), s));
+        TRYC(dev_alloc(&B.dbuf[1], bs * sizeof(gj_pair), s));
     }
     if (!count_only_call)
-        TRYC(cudaMalloc(&B.staging, (size_t)grid * stg_per_cta * sizeof(gj_pair)));
+        TRYC(dev_alloc(&B.staging, (size_t)grid * stg_per_cta * sizeof(gj_pair), s));
 
     // ---- 3. batch loop
     uint64_t written = 0, total = 0;
@@ -797,9 +864,12 @@ void gj_free(gj_index *h)
     dev_free(h->XB, s);
     dev_free(h->tc_centre, s);
     dev_free(h->perm_dev, s);
-    if (h->jd_ready) {
+    if (h->jd_ready || h->ss) {
         cudaStreamSynchronize(s);
-        free_direct_state(h);
+        if (h->jd_ready)
+            free_direct_state(h);
+        delete h->ss;
+        h->ss = nullptr;
     }
     if (h->drain_stream)
         cudaStreamDestroy(h->drain_stream);

@@ -242,6 +242,10 @@ int autotune_impl(const double *points, int64_t n, int d, double eps, const gj_c
 
 }  // namespace gj
 
+namespace gj {
+struct StagedState;   // gj_api.cu
+}
+
 // The handle (gj_api.cu)
 struct gj_index {
     int device;
@@ -290,4 +294,7 @@ struct gj_index {
     uint32_t *jd_queue;                      // device, one entry per work item
     unsigned long long *jd_span, *jd_hspan;  // per-SM spans: device, pinned host
     cudaEvent_t jd_ev0, jd_ev1;
+    // launch state of the staged join (result batches, plain form), allocated
+    // by the first such join on the handle and kept until gj_free
+    gj::StagedState *ss;
 };
