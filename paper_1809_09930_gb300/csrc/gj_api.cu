@@ -863,6 +863,7 @@ void gj_free(gj_index *h)
     dev_free(h->XA, s);
     dev_free(h->XB, s);
     dev_free(h->tc_centre, s);
+    dev_free(h->XR, s);
     dev_free(h->perm_dev, s);
     if (h->jd_ready || h->ss) {
         cudaStreamSynchronize(s);

@@ -205,8 +205,8 @@ cudaError_t tc_radius(const double *X, int64_t n, int64_t npad, int d, const dou
                       cudaStream_t s);
 double tc_sigma_for(double R0);
 // direct form over explicit operands (L.ix.asym: Q join_eps E)
-cudaError_t launch_join_tc_ops(const JoinLaunch &L, const void *XA, const void *XB, int Kp, int Tbits, int grid,
-                               cudaStream_t s);
+cudaError_t launch_join_tc_ops(const JoinLaunch &L, const void *XA, const void *XB, const double *XR, int dr, int Kp,
+                               int Tbits, int grid, cudaStream_t s);
 // job_cycles (nullable): per-job SM cycles between the epilogue's item ends,
 // summed over CTAs (the autotuner's per-job timing)
 cudaError_t launch_join_tc_jobs(const JoinLaunch &L, const void *XA, const void *XB, int Kp, const TcJob *jobs,
@@ -287,6 +287,8 @@ struct gj_index {
     int tc_Tbits;        // fp32 bits of the survivor threshold (scaled units)
     double tc_sigma, tc_R0;
     double *tc_centre;   // device, the filter's centre per reordered dimension
+    double *XR;          // device, the points row by row (n x XR_dr FP64) for the FP64 recheck
+    int XR_dr;
     // launch state of the tensor-core join's direct form, allocated by the
     // first such join on the handle and kept until gj_free
     bool jd_ready;

@@ -213,7 +213,8 @@ extern "C" int gj_join_qe(gj_index *h, const double *queries, int64_t nq, gj_pai
     if (e == cudaSuccess) e = cudaMemsetAsync(ctl, 0, sizeof(JoinCtl), s);
     if (e == cudaSuccess) e = cudaEventRecord(ev0, s);
     if (e == cudaSuccess)
-        e = tc ? launch_join_tc_ops(L, XAq, XBop, h->tc_Kp, Tbits, grid, s) : launch_join_plain_direct(L, grid, s);
+        e = tc ? launch_join_tc_ops(L, XAq, XBop, h->XR, h->XR_dr, h->tc_Kp, Tbits, grid, s)
+               : launch_join_plain_direct(L, grid, s);
     if (e == cudaSuccess) e = cudaEventRecord(ev1, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&hctl, ctl, sizeof(JoinCtl), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);

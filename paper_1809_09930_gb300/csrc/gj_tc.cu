@@ -137,6 +137,8 @@ struct TcLaunch {
     unsigned long long *job_cycles;   // many-jobs tuning launch: per-job SM cycles (else nullptr)
     const unsigned char *XA;
     const unsigned char *XB;
+    const double *XR;            // entries row by row for the recheck (nullptr: from X)
+    int dr;                      // XR's row stride in doubles
     int Kp;
     int NS;
     int Tbits;
@@ -176,19 +178,45 @@ __device__ __forceinline__ int64_t tc_upper_u(const double *__restrict__ U, int6
 // Coordinates are fetched 16 dimensions at a time with independent loads, so
 // a recheck costs about d/16 memory round trips instead of d.  The query
 // comes from Xq (the entries themselves in a self-join, the query array in
-// Q join_eps E), the candidate from the entries X.
+// Q join_eps E), the candidate from the entries X.  With XR (the entries row
+// by row, row stride dr a multiple of 4) the candidate's 16 coordinates are
+// 128 contiguous bytes, four 32-byte sectors where the structure-of-arrays
+// layout touches sixteen; in a self-join (qrows) the query is read there too.
 __device__ __forceinline__ bool tc_exact(const double *__restrict__ Xq, int64_t qnpad,
-                                         const double *__restrict__ X, int64_t npad, int d, long long e2bits,
-                                         uint32_t qpos, uint32_t cpos)
+                                         const double *__restrict__ X, int64_t npad,
+                                         const double *__restrict__ XR, int dr, bool qrows,
+                                         int d, long long e2bits, uint32_t qpos, uint32_t cpos)
 {
     double s = 0.0;
     for (int j0 = 0; j0 < d; j0 += 16) {
         double a[16], b[16];
+        if (XR) {
+            // (a row holds dr >= d values, d rounded up to 4: each pair is in it)
+            const double2 *rb = reinterpret_cast<const double2 *>(XR + (int64_t)cpos * dr + j0);
+            const double2 *ra = reinterpret_cast<const double2 *>(XR + (int64_t)qpos * dr + j0);
 #pragma unroll
-        for (int t = 0; t < 16; ++t) {
-            if (j0 + t < d) {
-                a[t] = Xq[(int64_t)(j0 + t) * qnpad + qpos];
-                b[t] = X[(int64_t)(j0 + t) * npad + cpos];
+            for (int t = 0; t < 8; ++t) {
+                if (j0 + 2 * t < d) {
+                    const double2 vb = __ldg(rb + t);
+                    b[2 * t] = vb.x;
+                    b[2 * t + 1] = vb.y;
+                    if (qrows) {
+                        const double2 va = __ldg(ra + t);
+                        a[2 * t] = va.x;
+                        a[2 * t + 1] = va.y;
+                    } else {
+                        a[2 * t] = Xq[(int64_t)(j0 + 2 * t) * qnpad + qpos];
+                        a[2 * t + 1] = Xq[(int64_t)min(j0 + 2 * t + 1, d - 1) * qnpad + qpos];
+                    }
+                }
+            }
+        } else {
+#pragma unroll
+            for (int t = 0; t < 16; ++t) {
+                if (j0 + t < d) {
+                    a[t] = Xq[(int64_t)(j0 + t) * qnpad + qpos];
+                    b[t] = X[(int64_t)(j0 + t) * npad + cpos];
+                }
             }
         }
 #pragma unroll
@@ -232,7 +260,7 @@ __device__ __noinline__ void tc_flush_survivors(const TcLaunch *__restrict__ T, 
         if (i < n) {
             qpos = sq[i];
             cpos = sc[i];
-            keep = tc_exact(Xq, qnpad, X, npad, d, e2bits, qpos, cpos);
+            keep = tc_exact(Xq, qnpad, X, npad, jp ? nullptr : T->XR, T->dr, !ASYM, d, e2bits, qpos, cpos);
         }
         const uint32_t np = keep ? ((!ASYM && qpos != cpos) ? 2u : 1u) : 0u;
         if (stg == nullptr && jp == nullptr && dpos == nullptr) {
@@ -1435,6 +1463,19 @@ __global__ void k_tc_pack(const double *__restrict__ X, int64_t n, int64_t npad,
     }
 }
 
+// XR[p * dr + j] = X[j * npad + p]: the points row by row (rows padded with
+// zeros to dr values), for the recheck's contiguous reads.
+__global__ void k_tc_rows(const double *__restrict__ X, int64_t n, int64_t npad, int d, int dr,
+                          double *__restrict__ XR)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n * dr)
+        return;
+    const int64_t p = i / dr;
+    const int j = (int)(i - p * dr);
+    XR[i] = j < d ? X[(int64_t)j * npad + p] : 0.0;
+}
+
 // Survivor threshold in scaled units (see the file header for the terms).
 double tc_threshold(double eps, double sigma, double R0, int d, int Kp)
 {
@@ -1483,6 +1524,16 @@ int tc_prepare(gj_index *h, const double *stats_host, const int *perm, cudaStrea
         k_tc_pack<<<(int)((n + 127) / 128), 128, 0, s>>>(h->X, n, h->npad, P, (uint4 *)h->XA, (uint4 *)h->XB);
         e = cudaGetLastError();
     }
+    // the recheck's copy of the points, row by row
+    const int dr = (d + 3) & ~3;
+    if (e == cudaSuccess)
+        e = dev_alloc(&h->XR, (size_t)n * dr * sizeof(double), s);
+    if (e == cudaSuccess) {
+        note_launch();
+        k_tc_rows<<<(int)((n * dr + 255) / 256), 256, 0, s>>>(h->X, n, h->npad, d, dr, h->XR);
+        e = cudaGetLastError();
+    }
+    h->XR_dr = dr;
     h->tc_centre = centre;   // kept: a many-jobs layout and Q join_eps E re-pack from it
     if (e != cudaSuccess)
         return e == cudaErrorMemoryAllocation ? GJ_ERR_OOM : GJ_ERR_CUDA;
@@ -1580,6 +1631,8 @@ cudaError_t launch_join_tc(const gj_index *h, const JoinLaunch &L, int grid, cud
     T.J = L;
     T.XA = (const unsigned char *)h->XA;
     T.XB = (const unsigned char *)h->XB;
+    T.XR = h->XR;
+    T.dr = h->XR_dr;
     T.Kp = h->tc_Kp;
     T.Tbits = h->tc_Tbits;
     T.limit_ns = wait_limit_ns();
@@ -1602,14 +1655,17 @@ cudaError_t launch_join_tc(const gj_index *h, const JoinLaunch &L, int grid, cud
 }
 
 // Direct form over explicit operand arrays and threshold (Q join_eps E: query
-// A rows, entry B rows, both under one centre and scale).
-cudaError_t launch_join_tc_ops(const JoinLaunch &L, const void *XA, const void *XB, int Kp, int Tbits, int grid,
-                               cudaStream_t s)
+// A rows, entry B rows, both under one centre and scale; XR: the entries row by
+// row, nullable).
+cudaError_t launch_join_tc_ops(const JoinLaunch &L, const void *XA, const void *XB, const double *XR, int dr, int Kp,
+                               int Tbits, int grid, cudaStream_t s)
 {
     TcLaunch T{};
     T.J = L;
     T.XA = (const unsigned char *)XA;
     T.XB = (const unsigned char *)XB;
+    T.XR = XR;
+    T.dr = dr;
     T.Kp = Kp;
     T.Tbits = Tbits;
     T.limit_ns = wait_limit_ns();
