@@ -712,9 +712,9 @@ def main():
         peak = pk.get("bf16_tflops_sustained") or pk.get("bf16_tflops")
         achieved = col["flops"] / join_s / 1e12
         # DRAM traffic of one 2M-point d = 32 launch: the ncu capture of a 1M-point launch of this
-        # kernel (8.11 GB: B-tile re-reads, mostly served from L2) scaled by its candidate pairs (x 4)
+        # kernel (3.53 GB: operand re-reads and recheck gathers) scaled by its candidate pairs (x 4)
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": 32.5e9 if args.workload == "paper" else None,
+                "frac": achieved / peak, "traffic": 14.1e9 if args.workload == "paper" else None,
                 "traffic_note": "bytes per d=32 launch at n=2e6, scaled from a 1e6-point ncu capture",
                 "kernel": "k_join_tc",
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (fp16 runs at the bf16 rate)",
