@@ -56,7 +56,10 @@ extern "C" {
 #define GJ_REORDER    (1u << 0)  /* Sec. 4.2: index the k highest-variance dimensions       */
 #define GJ_SORTIDU    (1u << 1)  /* Sec. 4.3: sort cells by one un-indexed dim, window search */
 #define GJ_SHORTC     (1u << 2)  /* Sec. 4.4: stop a distance once it exceeds eps^2          */
-#define GJ_TC_FILTER  (1u << 3)  /* tensor-core candidate filter + exact FP64 recheck (no paper counterpart) */
+#define GJ_TC_FILTER  (1u << 3)  /* tensor-core candidate filter + exact FP64 recheck (no paper counterpart);
+                                  * the index also holds the fp16 operand rows (2 x 2 x Kp bytes per
+                                  * point, Kp = d + 4 rounded up to 16) and a row-major FP64 copy of
+                                  * the points for the recheck (8 x (d rounded up to 4) bytes)        */
 #define GJ_AUTOTUNE   (1u << 4)  /* build: pick k, query block, tile and b_s by timed trials (gj_autotune) */
 #define GJ_TUNE_FORM  (1u << 5)  /* autotune: also try both forms (plain and GJ_TC_FILTER), keep the faster */
 #define GJ_HOST_BATCHED (1u << 6) /* host output always through the result batches of Sec. 3.2.2
